@@ -1,0 +1,359 @@
+"""Benchmark of the match-phase decode (output GB/s and fraction of the HBM
+roofline) on the synthetic copy sweep: 1 GiB of output generated directly
+as tokens, literal runs geometric (mean 4) of random bytes, matches of
+fixed length L (default 1024) from sources uniform in [0, pos - L), decoded
+with G-lane groups (Table II's experiment, Sec. III-C).
+
+One JSON line on rank 0.  `value` is device-resident decode throughput
+(container already in HBM); `e2e` is the same metric through the public C
+ABI from pinned host buffers, the upload (host->device copy and index
+build) and the read-back of the decoded bytes inside the timed region.
+`--impl reference` times the CPU oracle's sequential decoder instead, on a
+bounded sample of the same workload.
+
+Multi-GPU: the decode does not shard (absolute sources reach anywhere
+earlier), so N ranks run N independent replicas (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PAPER_H100 = {1024: 744, 512: 734, 256: 692, 128: 607, 64: 416, 32: 212}  # Table II, GB/s
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=1024)
+    ap.add_argument("--total", type=int, default=1 << 30)
+    ap.add_argument("--block-size", type=int, default=1 << 15)
+    ap.add_argument("--G", type=int, default=32)
+    ap.add_argument("--mode", default="waves", choices=["waves", "persistent"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(total, bs, L, seed_offset=0):
+    from paper_2607_18541_gb300 import synth
+    return synth.copy_sweep(total, bs, L, seed=synth.SEED_COPY + L + seed_offset)
+
+
+def algorithmic_bytes(sw) -> int:
+    """16 B per token + literal bytes read + match source bytes read +
+    output bytes written."""
+    match_bytes = int(sw.match_len.astype(np.int64).sum())
+    return 16 * sw.n_tokens + int(sw.literals.size) + match_bytes + int(sw.total)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_sources_sha() -> str:
+    d = os.path.join(ROOT, "paper_2607_18541_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """dram bytes per step from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload)
+    if not e or e.get("kernel_sources_sha") != kernel_sources_sha():
+        return None
+    return e.get("dram_bytes_per_step")
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+                power.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def cpu_baseline(args, seconds: float):
+    """The oracle's sequential decoder (one host thread) on a bounded sample
+    of the same workload: a 128 MiB copy sweep of the same recipe, decoded
+    repeatedly for about `seconds`."""
+    import oracle
+    sample = min(args.total, 128 << 20)
+    sw = make_workload(sample, args.block_size, args.L, seed_offset=1)
+    c = oracle.pack_sweep(sw, tags=False)
+    oracle.decode(c)  # warm
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.decode(c)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    gbs = n * sample / el / 1e9
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample >> 20} MiB copy sweep (L={args.L}, same recipe), decoded {n} times "
+                      f"in {el:.1f} s by the sequential oracle decoder"}
+
+
+def run_reference(args):
+    """The oracle's sequential decoder as the reference arm: W warm-up and K
+    timed decodes of a bounded sample of the same workload (a copy sweep of
+    the same recipe, at most 128 MiB, shrunk so K decodes take <= ~2 min)."""
+    import oracle
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    sample = min(args.total, 128 << 20)
+    sw = make_workload(sample, args.block_size, args.L, seed_offset=1)
+    c = oracle.pack_sweep(sw, tags=False)
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.warmup)):
+        oracle.decode(c)
+    per = (time.perf_counter() - t0) / max(1, args.warmup)
+    if per * args.steps > 120.0:
+        sample = max(1 << 20, int(sample * 120.0 / (per * args.steps)) & ~((1 << 20) - 1))
+        sw = make_workload(sample, args.block_size, args.L, seed_offset=1)
+        c = oracle.pack_sweep(sw, tags=False)
+        oracle.decode(c)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.decode(c)
+    el = time.perf_counter() - t0
+    gbs = args.steps * sample / el / 1e9
+    cb = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+          "sample": f"{sample >> 20} MiB copy sweep (L={args.L}, same recipe) per step, "
+                    f"{args.steps} steps in {el:.1f} s, sequential oracle decoder"}
+    line = {
+        "impl": "reference",
+        "metric": f"match-phase decode output GB/s (copy sweep, L={args.L})",
+        "value": cb["value"], "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8", "data": "synthetic",
+        "config": workload_config(args, None),
+        "cpu_baseline": cb,
+        "e2e": {"value": cb["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, extra):
+    cfg = {"workload": f"copy_sweep_{args.total >> 20}MiB_L{args.L}", "total_bytes": args.total,
+           "match_len": args.L, "lit_mean": 4, "block_size": args.block_size, "G": args.G,
+           "mode": args.mode, "lanes": args.G * ((args.total + args.block_size - 1) // args.block_size),
+           "l2": "flushed between timed steps (256 MiB write)" if not args.no_flush else "not flushed"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def run_ours(args):
+    import torch
+    from paper_2607_18541_gb300 import aclz
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    aclz.lib()
+    sw = make_workload(args.total, args.block_size, args.L, seed_offset=0)
+    c = aclz.aclz_pack(sw.total, sw.block_size, (4, 4, 4, 4), sw.blk_ntok, sw.lit_len, sw.match_len,
+                       sw.src, sw.literals)
+    abytes = algorithmic_bytes(sw)
+    mode = aclz.ACLZ_MODE_PERSISTENT if args.mode == "persistent" else aclz.ACLZ_MODE_WAVES
+    st = torch.cuda.Stream(device=dev)
+    h = aclz.aclz_upload(c, st)
+    info = aclz.aclz_handle_info(h)
+    counts = aclz.aclz_wave_counts(h)
+    launches_per_step = 1 if mode == aclz.ACLZ_MODE_PERSISTENT else 1 + int((counts[1:] > 0).sum())
+    out = torch.empty(((sw.total + 15) // 16) * 16, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        aclz.aclz_decode_all(h, out, G=args.G, mode=mode, stream=st)
+
+    with torch.cuda.stream(st):
+        for _ in range(args.warmup):
+            step()
+        st.synchronize()
+        assert aclz.aclz_device_status(h, st) == 0
+        # correctness of what we time: FNV of the output against the oracle is
+        # the test suite's job; here a cheap self-check of the decoded size
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        clk = ClockSampler(local)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clk.start()
+        time.sleep(0.2)
+        t_wall0 = time.perf_counter()
+        for i in range(args.steps):
+            if not args.no_flush:
+                flush.fill_(i & 0xff)
+            starts[i].record(st)
+            step()
+            ends[i].record(st)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+        clocks = clk.stop()
+        if world > 1:
+            torch.distributed.barrier()
+    assert aclz.aclz_device_status(h, st) == 0
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_step = sum(ms) / len(ms)
+    t = torch.tensor([ms_step], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * sw.total / (ms_max * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    achieved = abytes / (ms_step * 1e-3) / 1e9
+    workload = workload_config(args, None)["workload"]
+    traffic = recorded_traffic(workload)
+
+    # end to end through the C ABI from pinned host memory
+    host_c = torch.from_numpy(c).pin_memory()
+    host_out = torch.empty(sw.total, dtype=torch.uint8).pin_memory()
+    e2e_ms = []
+    with torch.cuda.stream(st):
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hh = aclz.aclz_upload(host_c.numpy(), st)
+            aclz.aclz_decode_all(hh, out, G=args.G, mode=mode, stream=st)
+            host_out.copy_(out[:sw.total], non_blocking=True)
+            st.synchronize()
+            dt = time.perf_counter() - t0
+            aclz.aclz_free(hh)
+            if i:
+                e2e_ms.append(dt * 1e3)
+    e2e_val = world * sw.total / (statistics.mean(e2e_ms) * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": f"match-phase decode output GB/s (copy sweep, L={args.L})",
+            "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": workload_config(args, {"n_waves": info.n_waves, "n_tokens": info.n_tokens,
+                                             "n_deferred": info.n_deferred,
+                                             "algorithmic_bytes_per_step": abytes}),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "unit_of_launch": "one decode step (all kernels of one decode_all call)",
+                         "peak_kind": f"{peak_kind} (copy, burst)"},
+            "clocks": clocks,
+            "gpu_launches": launches_per_step * args.steps,
+            "e2e": {"value": round(e2e_val, 2), "unit": "GB/s", "h2d_bytes_per_step": int(c.size),
+                    "d2h_bytes_per_step": int(sw.total), "steps": args.e2e_steps},
+            "paper_h100_context": {"value": PAPER_H100.get(args.L), "unit": "GB/s",
+                                   "what": "purecopy.cu synthetic copy, 1 GB, H100 (Table II)"},
+            "wall_s_timed": round(t_wall, 3),
+        }
+        if world == 1:
+            line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    aclz.aclz_free(h)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * aclz — device-resident match phase of absolute-offset LZ77 decode on
+ * GB300 (sm_103a).  C ABI of libaclz.so.
+ *
+ * The codec follows the paper "What Governs Decode Throughput in
+ * Absolute-Offset GPU LZ77?": back-references are absolute output positions
+ * (abstract; Sec. I), LZ blocks fixed at encode time are the unit of decode
+ * parallelism (Sec. II), minimum match lengths are set per distance class
+ * (Sec. IV-B), matches whose sources are not yet written are decoded in
+ * later waves (Sec. I), and results are verified by byte compare and FNV
+ * (abstract; Sec. II).
+ *
+ * Conventions for every entry point:
+ *  - Return value: ACLZ_OK (0) or a negative ACLZ_E_* code; aclz_strerror()
+ *    names it.  Nothing is allocated or launched when an argument is
+ *    rejected.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Decode calls only enqueue work; errors found on the device
+ *    (a bounded wait that ran out) are latched in the handle and returned
+ *    by aclz_device_status().
+ *  - Pointers named host_* are host memory, d_* are device memory of the
+ *    current CUDA device.  The caller owns every buffer it passes; the
+ *    library owns the device copies it makes in aclz_upload() until
+ *    aclz_free().
+ *  - Device output buffers must be 16-byte aligned.  Kernels write only
+ *    [d_out, d_out + length); they may read (never write) bytes up to the
+ *    end of the 16-byte word holding the last output byte.
+ *
+ * Container format v1 (little endian; the paper gives no byte layout, this
+ * is the reading the library and its oracle agree on):
+ *   header 64 B : "ACLZ", u16 version=1, u16 flags (bit0: wave tags
+ *                 present), u64 total_len, u32 block_size, u32 n_blocks,
+ *                 u64 n_tokens, u64 n_literals, u32 n_waves, u8 min_match[4],
+ *                 u32 distance bounds[3] = {128, 16384, 2097152}, u32 0
+ *   directory   : n_blocks x 32 B: u64 tok_off, u64 lit_off, u32 n_tok,
+ *                 u16 max_wave, u16 flags, u8 min_match[4], u32 0
+ *   tokens      : n_tokens x 16 B: u32 lit_len, u32 match_len,
+ *                 u64 (src : 40 bits | wave : 24 bits)
+ *   literals    : n_literals bytes
+ * Block b covers output [b*block_size, min((b+1)*block_size, total_len)).
+ * A token appends lit_len literals, then match_len bytes copied from
+ * absolute position src, with src + match_len <= the match's own position;
+ * match_len == 0 only on a block's last token.
+ */
+#ifndef ACLZ_H
+#define ACLZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ACLZ_OK 0
+#define ACLZ_E_INVAL (-1)       /* bad argument */
+#define ACLZ_E_CORRUPT (-2)     /* container fails validation */
+#define ACLZ_E_NOMEM (-3)       /* host or device allocation failed */
+#define ACLZ_E_CAPACITY (-4)    /* output or scratch buffer too small */
+#define ACLZ_E_CUDA (-5)        /* a CUDA runtime call failed */
+#define ACLZ_E_TIMEOUT (-6)     /* a bounded device-side wait ran out */
+#define ACLZ_E_DEVICE (-7)      /* another device-side error was latched */
+#define ACLZ_E_UNSUPPORTED (-8) /* valid container this build cannot decode */
+
+/* Encoder parameters (Sec. II: block size set at encode time; Sec. IV-B:
+ * minimum match length per distance class d < 128, < 16384, < 2097152,
+ * >= 2097152).  block_size: power of two, 64 B .. 16 MiB.  min_match >= 4.
+ * chain_depth: candidates examined per position.  window: largest match
+ * distance considered. */
+typedef struct aclz_encode_params {
+    uint32_t block_size;
+    uint8_t min_match[4];
+    uint32_t chain_depth;
+    uint32_t flags; /* reserved, 0 */
+    uint64_t window;
+} aclz_encode_params;
+
+#define ACLZ_PRESET_BASE 0  /* 6/8/10/12 (Sec. IV-B) */
+#define ACLZ_PRESET_TUNED 1 /* 12/16/24/32 (Sec. IV-B) */
+#define ACLZ_PRESET_PUSH 2  /* 16/24/32/48 (Sec. IV-C) */
+
+/* Fill *p with a preset: block_size 65536, chain_depth 64, unbounded
+ * window.  Returns ACLZ_E_INVAL for an unknown preset or NULL p. */
+int aclz_encode_params_default(aclz_encode_params *p, int preset);
+
+/* Upper bound of the container size for n input bytes. */
+uint64_t aclz_encode_bound(uint64_t n, uint32_t block_size);
+
+/* Greedy encoder on the host (the paper's encoder is a CPU program,
+ * Sec. VI).  At each position with >= 4 bytes left, the candidates are the
+ * earlier positions with the same 4-byte prefix, nearest first, up to
+ * chain_depth of them within the window; the longest candidate whose
+ * length (capped at the distance and at the block end) meets its distance
+ * class minimum wins, ties to the nearest.  block_min_match (4 bytes per
+ * block, or NULL) overrides the thresholds block by block.  threads <= 0
+ * uses all host cores.  The container carries no wave tags (aclz_upload
+ * computes them).  *out_size receives the container size. */
+int aclz_encode(const void *host_src, uint64_t n, const aclz_encode_params *p,
+                const uint8_t *block_min_match, int threads, void *host_out, uint64_t cap,
+                uint64_t *out_size);
+
+/* Container from token arrays (host): blk_ntok[n_blocks] tokens per
+ * block, lit_len/match_len/src per token, the literal bytes.  min_match is
+ * recorded, not enforced.  No wave tags. */
+int aclz_pack(uint64_t total_len, uint32_t block_size, const uint8_t min_match[4],
+              const uint32_t *blk_ntok, const uint32_t *lit_len, const uint32_t *match_len,
+              const uint64_t *src, uint64_t n_tokens, const uint8_t *literals,
+              uint64_t n_literals, void *host_out, uint64_t cap, uint64_t *out_size);
+
+/* Size of the container aclz_pack writes. */
+uint64_t aclz_pack_bytes(uint64_t total_len, uint32_t block_size, uint64_t n_tokens,
+                         uint64_t n_literals);
+
+typedef struct aclz_info {
+    uint64_t total_len, n_tokens, n_literals, n_deferred;
+    uint32_t block_size, n_blocks, n_waves, flags;
+    uint8_t min_match[4];
+    uint32_t reserved;
+} aclz_info;
+
+/* Header fields of a host container (checks magic, version and sizes). */
+int aclz_container_info(const void *host_buf, uint64_t n, aclz_info *out);
+
+typedef struct aclz_handle aclz_handle;
+
+/* Copy a host container to the current device and build its decode index
+ * on the GPU: validation of every token (lengths sum to the block length,
+ * src + match_len <= dst), wave tags (the minimal legal tags when the
+ * container has none; a legality check when it has them), and the
+ * wave-ordered worklist slots of deferred matches.  Synchronizes the
+ * stream.  ACLZ_E_CORRUPT for an invalid container. */
+int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_handle **out);
+
+/* Free a handle and its device memory (after its work has completed). */
+int aclz_free(aclz_handle *h);
+
+int aclz_handle_info(const aclz_handle *h, aclz_info *out);
+
+/* Per-wave deferred-match counts (wave 0 holds literals and in-order
+ * matches and reports 0); writes min(cap, n_waves) values. */
+int aclz_wave_counts(const aclz_handle *h, uint64_t *counts, uint32_t cap);
+
+/* Wave tags as computed or validated at upload (one per token), copied
+ * to host memory. */
+int aclz_tags(const aclz_handle *h, uint32_t *host_tags, uint64_t cap);
+
+typedef struct aclz_decode_cfg {
+    uint32_t G;           /* cooperating lanes per group: 8, 16 or 32 */
+    uint32_t mode;        /* ACLZ_MODE_WAVES or ACLZ_MODE_PERSISTENT */
+    uint32_t ctas_per_sm; /* persistent mode: resident CTAs per SM (0 = max) */
+    uint32_t flags;       /* reserved, 0 */
+} aclz_decode_cfg;
+
+#define ACLZ_MODE_WAVES 0      /* one kernel per wave */
+#define ACLZ_MODE_PERSISTENT 1 /* one launch, bounded per-block waits */
+
+/* Decode the whole stream into d_out (cap >= total_len bytes, 16-byte
+ * aligned).  Enqueues on stream; capturable in a CUDA graph (no allocation,
+ * no synchronization).  cfg NULL = {32, ACLZ_MODE_WAVES, 0, 0}. */
+int aclz_decode_all(aclz_handle *h, void *d_out, uint64_t cap, const aclz_decode_cfg *cfg,
+                    void *stream);
+
+/* Synchronize stream and return the device status latched by decode
+ * calls on h since the last call (ACLZ_OK, ACLZ_E_TIMEOUT, ACLZ_E_DEVICE). */
+int aclz_device_status(aclz_handle *h, void *stream);
+
+/* FNV-1a 64 of each 64 KiB chunk of d_buf, then FNV-1a 64 of the chunk
+ * hashes (8 LE bytes each) followed by n (8 LE bytes).  Synchronous:
+ * *out_hash holds the result on return.  Allocates stream-ordered scratch
+ * of 8 bytes per chunk. */
+int aclz_fnv(const void *d_buf, uint64_t n, uint64_t *out_hash, void *stream);
+
+const char *aclz_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACLZ_H */

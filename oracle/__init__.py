@@ -70,7 +70,7 @@ def lib() -> ctypes.CDLL:
             L.oracle_container_bytes.argtypes = [c_u64, c_u32, c_u64, c_u64]
             L.oracle_container_bytes.restype = c_u64
             L.oracle_pack.argtypes = [c_u64, c_u32, u8p, u32p, u32p, u32p, u64p, c_u64, u8p, c_u64,
-                                      u8p, c_u64]
+                                      u8p, c_u64, ctypes.c_int]
             L.oracle_pack.restype = ctypes.c_int64
             L.oracle_encode.argtypes = [u8p, c_u64, c_u32, u8p, u8p, c_u32, c_u64, u8p, c_u64]
             L.oracle_encode.restype = ctypes.c_int64
@@ -128,8 +128,8 @@ def encode(x, block_size: int, mm=PRESET_BASE, block_mm=None, chain_depth: int =
 
 
 def pack(total_len: int, block_size: int, blk_ntok, lit_len, match_len, src, literals,
-         mm=(4, 4, 4, 4)) -> np.ndarray:
-    """Container from token arrays, with minimal wave tags."""
+         mm=(4, 4, 4, 4), tags: bool = True) -> np.ndarray:
+    """Container from token arrays, with minimal wave tags unless tags=False."""
     blk = np.ascontiguousarray(blk_ntok, dtype=np.uint32)
     ll = np.ascontiguousarray(lit_len, dtype=np.uint32)
     ml = np.ascontiguousarray(match_len, dtype=np.uint32)
@@ -143,15 +143,15 @@ def pack(total_len: int, block_size: int, blk_ntok, lit_len, match_len, src, lit
                            ll.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
                            ml.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
                            sr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), ll.size, _u8(lits), nl,
-                           _u8(out), cap)
+                           _u8(out), cap, 1 if tags else 0)
     size = _check(int(rc), "pack")
     return out[:size].copy()
 
 
-def pack_sweep(sweep) -> np.ndarray:
+def pack_sweep(sweep, tags: bool = True) -> np.ndarray:
     """Container of a generated copy sweep (``synth.copy_sweep``)."""
     return pack(sweep.total, sweep.block_size, sweep.blk_ntok, sweep.lit_len, sweep.match_len,
-                sweep.src, sweep.literals)
+                sweep.src, sweep.literals, tags=tags)
 
 
 # ------------------------------------------------------------------ decode

@@ -296,11 +296,13 @@ int oracle_retag(uint8_t *c, uint64_t clen, const uint32_t *extra) {
     return OR_OK;
 }
 
-/* clear the tags of a container (flag off, all tags 0, wave count 0) */
+/* clear the tags of a container (flag off, all tags 0, wave count 0,
+ * per-block max wave 0) */
 int oracle_strip_tags(uint8_t *c, uint64_t clen) {
     or_view v;
     int rc = or_parse(c, clen, &v);
     if (rc) return rc;
+    for (uint32_t b = 0; b < v.n_blocks; b++) wr16(c + OR_HDR + (uint64_t)OR_DIRENT * b + 20, 0);
     uint8_t *tok = c + (v.tok - c);
     for (uint64_t i = 0; i < v.n_tokens; i++) {
         uint8_t *p = tok + (uint64_t)OR_TOK * i;
@@ -336,12 +338,14 @@ static void or_write_header(uint8_t *c, uint64_t total_len, uint32_t bs, uint32_
 }
 
 /* Assemble a container from token arrays (blk_ntok per block; lit_len,
- * match_len, src per token; the literal bytes) and give it minimal tags.
- * Returns the container size or a negative error. */
+ * match_len, src per token; the literal bytes) and, when with_tags, give it
+ * minimal tags (without tags the wave flag stays clear; the per-byte tag
+ * pass needs 4 bytes per output byte).  Returns the container size or a
+ * negative error. */
 int64_t oracle_pack(uint64_t total_len, uint32_t block_size, const uint8_t mm[4],
                     const uint32_t *blk_ntok, const uint32_t *lit_len, const uint32_t *match_len,
                     const uint64_t *src, uint64_t n_tokens, const uint8_t *literals,
-                    uint64_t n_literals, uint8_t *out, uint64_t cap) {
+                    uint64_t n_literals, uint8_t *out, uint64_t cap, int with_tags) {
     if (block_size == 0 || block_size % 16) return OR_E_INVAL;
     uint64_t nb = (total_len + block_size - 1) / block_size;
     if (nb > 0xffffffffULL) return OR_E_INVAL;
@@ -368,6 +372,7 @@ int64_t oracle_pack(uint64_t total_len, uint32_t block_size, const uint8_t mm[4]
     }
     if (t != n_tokens || l != n_literals) return OR_E_INVAL;
     memcpy(lit, literals, n_literals);
+    if (!with_tags) return (int64_t)need;
     int rc = oracle_retag(out, need, NULL);
     if (rc) return rc;
     /* per-block max wave, informational */
@@ -506,7 +511,7 @@ int64_t oracle_encode(const uint8_t *x, uint64_t n, uint32_t block_size, const u
         }
         bn[b] = cnt;
     }
-    int64_t rc = oracle_pack(n, block_size, mm, bn, ll, ml, sr, nt, lits, nl, out, cap);
+    int64_t rc = oracle_pack(n, block_size, mm, bn, ll, ml, sr, nt, lits, nl, out, cap, 1);
     if (rc > 0 && block_mm) {
         for (uint64_t b = 0; b < nb; b++) memcpy(out + OR_HDR + OR_DIRENT * b + 24, block_mm + 4 * b, 4);
     }

@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libaclz.so (include/aclz.h), same names as the
+C ABI.  Argument marshalling only: every decode step runs in the library's
+CUDA kernels.  Device buffers may be given as torch CUDA tensors or raw
+integer pointers; streams as torch.cuda.Stream, raw handles or None.
+
+There is no fallback: if libaclz.so is missing or fails to load, every call
+raises ``AclzError``.  Build it with ``paper_2607_18541_gb300.build.build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaclz.so")
+_lock = threading.Lock()
+_lib = None
+
+ACLZ_OK = 0
+ACLZ_E_INVAL = -1
+ACLZ_E_CORRUPT = -2
+ACLZ_E_NOMEM = -3
+ACLZ_E_CAPACITY = -4
+ACLZ_E_CUDA = -5
+ACLZ_E_TIMEOUT = -6
+ACLZ_E_DEVICE = -7
+ACLZ_E_UNSUPPORTED = -8
+ACLZ_PRESET_BASE, ACLZ_PRESET_TUNED, ACLZ_PRESET_PUSH = 0, 1, 2
+ACLZ_MODE_WAVES, ACLZ_MODE_PERSISTENT = 0, 1
+
+
+class AclzError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        msg = aclz_strerror(code) if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})")
+        self.code = code
+
+
+class aclz_encode_params(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_uint32), ("min_match", ctypes.c_uint8 * 4),
+                ("chain_depth", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("window", ctypes.c_uint64)]
+
+
+class aclz_info(ctypes.Structure):
+    _fields_ = [("total_len", ctypes.c_uint64), ("n_tokens", ctypes.c_uint64),
+                ("n_literals", ctypes.c_uint64), ("n_deferred", ctypes.c_uint64),
+                ("block_size", ctypes.c_uint32), ("n_blocks", ctypes.c_uint32),
+                ("n_waves", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("min_match", ctypes.c_uint8 * 4), ("reserved", ctypes.c_uint32)]
+
+
+class aclz_decode_cfg(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_uint32), ("mode", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+# (name, restype, argtypes)
+_VP, _U64, _U32, _I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+_U8P = ctypes.POINTER(ctypes.c_uint8)
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+_SIGS = [
+    ("aclz_encode_params_default", _I, [ctypes.POINTER(aclz_encode_params), _I]),
+    ("aclz_encode_bound", _U64, [_U64, _U32]),
+    ("aclz_encode", _I, [_VP, _U64, ctypes.POINTER(aclz_encode_params), _U8P, _I, _VP, _U64, _U64P]),
+    ("aclz_pack", _I, [_U64, _U32, _U8P, _U32P, _U32P, _U32P, _U64P, _U64, _U8P, _U64, _VP, _U64, _U64P]),
+    ("aclz_pack_bytes", _U64, [_U64, _U32, _U64, _U64]),
+    ("aclz_container_info", _I, [_VP, _U64, ctypes.POINTER(aclz_info)]),
+    ("aclz_upload", _I, [_VP, _U64, _VP, ctypes.POINTER(_VP)]),
+    ("aclz_free", _I, [_VP]),
+    ("aclz_handle_info", _I, [_VP, ctypes.POINTER(aclz_info)]),
+    ("aclz_wave_counts", _I, [_VP, _U64P, _U32]),
+    ("aclz_tags", _I, [_VP, _U32P, _U64]),
+    ("aclz_decode_all", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP]),
+    ("aclz_device_status", _I, [_VP, _VP]),
+    ("aclz_fnv", _I, [_VP, _U64, _U64P, _VP]),
+    ("aclz_strerror", ctypes.c_char_p, [_I]),
+]
+OPTIONAL_SIGS: list = []  # entry points added by later modules register here
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise AclzError(ACLZ_E_UNSUPPORTED, f"libaclz.so not built at {LIB_PATH}")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, res, args in _SIGS + OPTIONAL_SIGS:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def exported_names() -> list[str]:
+    return [s[0] for s in _SIGS + OPTIONAL_SIGS]
+
+
+def _ck(rc: int, what: str) -> int:
+    if rc < 0:
+        raise AclzError(int(rc), what)
+    return rc
+
+
+def _dptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _hptr(a: np.ndarray) -> int:
+    return int(a.ctypes.data)
+
+
+def _np_u8(x) -> np.ndarray:
+    if isinstance(x, (bytes, bytearray)):
+        return np.frombuffer(bytes(x), dtype=np.uint8)
+    return np.ascontiguousarray(x).view(np.uint8).reshape(-1)
+
+
+# ------------------------------------------------------------------ encode
+
+def aclz_strerror(code: int) -> str:
+    return lib().aclz_strerror(code).decode()
+
+
+def aclz_encode_params_default(preset: int = ACLZ_PRESET_BASE) -> aclz_encode_params:
+    p = aclz_encode_params()
+    _ck(lib().aclz_encode_params_default(ctypes.byref(p), preset), "aclz_encode_params_default")
+    return p
+
+
+def aclz_encode_bound(n: int, block_size: int) -> int:
+    return int(lib().aclz_encode_bound(n, block_size))
+
+
+def aclz_encode(src, params: aclz_encode_params, block_min_match=None, threads: int = 0) -> np.ndarray:
+    x = _np_u8(src)
+    cap = aclz_encode_bound(x.size, params.block_size)
+    out = np.empty(cap, dtype=np.uint8)
+    size = ctypes.c_uint64(0)
+    bmm = None
+    if block_min_match is not None:
+        bmm = np.ascontiguousarray(block_min_match, dtype=np.uint8).reshape(-1)
+    _ck(lib().aclz_encode(_hptr(x) if x.size else None, x.size, ctypes.byref(params),
+                          None if bmm is None else bmm.ctypes.data_as(_U8P), threads, _hptr(out), cap,
+                          ctypes.byref(size)), "aclz_encode")
+    return out[:size.value]
+
+
+def aclz_pack_bytes(total_len: int, block_size: int, n_tokens: int, n_literals: int) -> int:
+    return int(lib().aclz_pack_bytes(total_len, block_size, n_tokens, n_literals))
+
+
+def aclz_pack(total_len: int, block_size: int, min_match, blk_ntok, lit_len, match_len, src,
+              literals) -> np.ndarray:
+    blk = np.ascontiguousarray(blk_ntok, dtype=np.uint32)
+    ll = np.ascontiguousarray(lit_len, dtype=np.uint32)
+    ml = np.ascontiguousarray(match_len, dtype=np.uint32)
+    sr = np.ascontiguousarray(src, dtype=np.uint64)
+    lits = _np_u8(literals)
+    mm = (ctypes.c_uint8 * 4)(*min_match)
+    cap = aclz_pack_bytes(total_len, block_size, ll.size, lits.size)
+    out = np.empty(cap, dtype=np.uint8)
+    size = ctypes.c_uint64(0)
+    _ck(lib().aclz_pack(total_len, block_size, mm, blk.ctypes.data_as(_U32P), ll.ctypes.data_as(_U32P),
+                        ml.ctypes.data_as(_U32P), sr.ctypes.data_as(_U64P), ll.size,
+                        lits.ctypes.data_as(_U8P) if lits.size else None, lits.size, _hptr(out), cap,
+                        ctypes.byref(size)), "aclz_pack")
+    return out[:size.value]
+
+
+def aclz_container_info(buf) -> aclz_info:
+    c = _np_u8(buf)
+    info = aclz_info()
+    _ck(lib().aclz_container_info(_hptr(c), c.size, ctypes.byref(info)), "aclz_container_info")
+    return info
+
+
+# ------------------------------------------------------------------ device
+
+def aclz_upload(buf, stream=None) -> int:
+    """Returns the handle as an integer."""
+    c = _np_u8(buf)
+    h = ctypes.c_void_p(0)
+    _ck(lib().aclz_upload(_hptr(c), c.size, _stream(stream), ctypes.byref(h)), "aclz_upload")
+    return int(h.value)
+
+
+def aclz_free(h: int) -> None:
+    _ck(lib().aclz_free(h), "aclz_free")
+
+
+def aclz_handle_info(h: int) -> aclz_info:
+    info = aclz_info()
+    _ck(lib().aclz_handle_info(h, ctypes.byref(info)), "aclz_handle_info")
+    return info
+
+
+def aclz_wave_counts(h: int) -> np.ndarray:
+    nw = aclz_handle_info(h).n_waves
+    out = np.zeros(max(1, nw), dtype=np.uint64)
+    _ck(lib().aclz_wave_counts(h, out.ctypes.data_as(_U64P), nw), "aclz_wave_counts")
+    return out[:nw]
+
+
+def aclz_tags(h: int) -> np.ndarray:
+    nt = aclz_handle_info(h).n_tokens
+    out = np.zeros(max(1, nt), dtype=np.uint32)
+    _ck(lib().aclz_tags(h, out.ctypes.data_as(_U32P), nt), "aclz_tags")
+    return out[:nt]
+
+
+def aclz_decode_all(h: int, d_out, cap: int | None = None, G: int = 32, mode: int = ACLZ_MODE_WAVES,
+                    ctas_per_sm: int = 0, stream=None) -> None:
+    if cap is None:
+        cap = int(d_out.numel() * d_out.element_size())
+    cfg = aclz_decode_cfg(G, mode, ctas_per_sm, 0)
+    _ck(lib().aclz_decode_all(h, _dptr(d_out), cap, ctypes.byref(cfg), _stream(stream)), "aclz_decode_all")
+
+
+def aclz_device_status(h: int, stream=None) -> int:
+    return _ck(lib().aclz_device_status(h, _stream(stream)), "aclz_device_status")
+
+
+def aclz_fnv(d_buf, n: int | None = None, stream=None) -> int:
+    if n is None:
+        n = int(d_buf.numel() * d_buf.element_size())
+    out = ctypes.c_uint64(0)
+    _ck(lib().aclz_fnv(_dptr(d_buf), n, ctypes.byref(out), _stream(stream)), "aclz_fnv")
+    return int(out.value)

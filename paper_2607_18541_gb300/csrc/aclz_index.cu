@@ -1,0 +1,576 @@
+// Upload of a container and construction of its decode index on the GPU.
+//
+//  1. k_index_scan   per block: prefix-sum of token lengths, per-token
+//                    validation (lengths fill the block, every source lies
+//                    strictly before its target, Sec. I), block-relative
+//                    token offsets for the seek path.
+//  2. k_tags_min     minimal wave tags (a match waits one wave for every
+//                    cross-block hop of its source chain; same-block sources
+//                    are ordered within the block), computed in one launch:
+//                    blocks are taken in increasing order and a block waits
+//                    (bounded) for the earlier blocks its sources lie in.
+//     k_tags_check   legality of tags supplied by the container.
+//  3. k_wave_hist, an exclusive scan and k_slots: the wave-major, block-
+//     ordered worklist slot of every deferred match.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "aclz_device.cuh"
+#include "aclz_internal.h"
+
+using namespace aclz;
+
+namespace {
+
+constexpr uint32_t kSpinLimit = 1u << 24;  // bounded waits (x ~64-256 ns)
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------- scan
+__global__ void __launch_bounds__(256) k_index_scan(const uint4 *__restrict__ tok,
+                                                    const uint64_t *__restrict__ blk_tok,
+                                                    const uint64_t *__restrict__ blk_lit,
+                                                    uint32_t *__restrict__ tokdst, uint32_t nb,
+                                                    uint32_t log2bs, uint64_t total, int has_tags,
+                                                    uint32_t *err, unsigned long long *first_bad) {
+    Group<32> g;
+    const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nb) return;
+    const uint64_t t0 = blk_tok[b], t1 = blk_tok[b + 1];
+    const uint64_t bstart = (uint64_t)b << log2bs;
+    const uint64_t blen = min((uint64_t)1 << log2bs, total - bstart);
+    uint64_t carry = 0, lcarry = 0;
+    bool bad = false;
+    for (uint64_t w = t0; w < t1; w += 32) {
+        const uint64_t i = w + g.lane;
+        const bool v = i < t1;
+        uint4 t = v ? __ldg(tok + i) : make_uint4(0, 0, 0, 0);
+        const uint64_t lit = t.x, ml = t.y;
+        const uint64_t sw = (uint64_t)t.z | ((uint64_t)t.w << 32);
+        const uint64_t tot = lit + ml;
+        const uint64_t incl = g.scan_incl(tot);
+        const uint64_t rel = carry + incl - tot;
+        const uint64_t lsum = g.scan_incl(lit);
+        if (v) {
+            bool ok = rel + tot <= blen;
+            if (ml == 0) {
+                ok = ok && (i == t1 - 1) && sw == 0;
+            } else {
+                const uint64_t src = sw & kSrcMask;
+                const uint64_t dm = bstart + rel + lit;
+                ok = ok && ml < (1u << 24) && src + ml <= dm;
+                if (!has_tags) ok = ok && (sw >> 40) == 0;
+            }
+            if (!ok) {
+                bad = true;
+                atomicMin(first_bad, (unsigned long long)i);
+            }
+            tokdst[i] = (uint32_t)rel;
+        }
+        carry += g.shfl(incl, 31);
+        lcarry += g.shfl(lsum, 31);
+    }
+    if (g.lane == 0 && (carry != blen || blk_lit[b] + lcarry != blk_lit[b + 1])) bad = true;
+    if (g.ballot(bad) && g.lane == 0) atomicOr(err, kErrCorrupt);
+}
+
+// Requirement of match i under the current tags: max over the tokens its
+// source range overlaps of (0 for literal bytes, tag for match bytes) plus
+// one when that token lies in another block.  Sets *inwin when a covering
+// token has index >= win0 (same window, still being resolved).
+__device__ uint32_t match_requirement(const uint4 *__restrict__ tok, const uint64_t *__restrict__ blk_tok,
+                                      const uint32_t *__restrict__ tokdst, const uint32_t *tags,
+                                      uint64_t src, uint64_t ml, uint32_t b, uint32_t log2bs,
+                                      uint64_t n_tok, uint64_t win0, bool *inwin) {
+    uint64_t bp = src >> log2bs;
+    uint64_t lo = blk_tok[bp], hi = blk_tok[bp + 1] - 1;
+    const uint32_t rel = (uint32_t)(src - (bp << log2bs));
+    // last token of block bp with tokdst <= rel
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(tokdst + mid) <= rel) lo = mid; else hi = mid - 1;
+    }
+    uint64_t t = lo;
+    uint64_t bend_tok = blk_tok[bp + 1];
+    const uint64_t e = src + ml;
+    uint32_t req = 0;
+    for (;;) {
+        const uint64_t ts = (bp << log2bs) + __ldg(tokdst + t);
+        if (ts >= e) break;
+        const uint4 tk = __ldg(tok + t);
+        const uint32_t cross = (bp != b) ? 1u : 0u;
+        const uint64_t le = ts + tk.x;  // end of literal part
+        if (tk.x && le > src) req = max(req, cross);
+        if (tk.y && le < e && le + tk.y > src) {
+            const uint32_t tg = __ldcg(tags + t);
+            req = max(req, tg + cross);
+            if (t >= win0) *inwin = true;
+        }
+        t++;
+        if (t >= n_tok) break;
+        if (t >= bend_tok) {
+            bp++;
+            bend_tok = blk_tok[bp + 1];
+        }
+    }
+    return req;
+}
+
+// Minimal tags.  Warps take blocks in increasing order from a counter; a
+// block's matches whose sources lie in earlier blocks wait (bounded) for
+// those blocks' done flags; in-window dependencies are resolved by
+// iterating the window to its fixed point.
+__global__ void __launch_bounds__(256) k_tags_min(const uint4 *__restrict__ tok,
+                                                  const uint64_t *__restrict__ blk_tok,
+                                                  const uint32_t *__restrict__ tokdst,
+                                                  uint32_t *tags, uint32_t *done, uint32_t *ctr,
+                                                  uint32_t nb, uint32_t log2bs, uint64_t n_tok,
+                                                  uint32_t *maxtag, uint32_t *err) {
+    Group<32> g;
+    for (;;) {
+        uint32_t b = 0;
+        if (g.lane == 0) b = atomicAdd(ctr, 1u);
+        b = g.shfl(b, 0);
+        if (b >= nb) return;
+        const uint64_t t0 = blk_tok[b], t1 = blk_tok[b + 1];
+        uint32_t mx = 0;
+        bool timed_out = false;
+        for (uint64_t w = t0; w < t1; w += 32) {
+            const uint64_t i = w + g.lane;
+            const bool v = i < t1;
+            uint4 t = v ? __ldg(tok + i) : make_uint4(0, 0, 0, 0);
+            const uint64_t ml = t.y;
+            const uint64_t src = ((uint64_t)t.z | ((uint64_t)t.w << 32)) & kSrcMask;
+            const bool m = v && ml;
+            if (v) __stcg(tags + i, 0u);
+            // wait for the earlier blocks this match reads
+            if (m) {
+                const uint64_t b0 = src >> log2bs, b1 = (src + ml - 1) >> log2bs;
+                for (uint64_t bb = b0; bb <= b1 && bb < b; bb++) {
+                    uint32_t spins = 0;
+                    while (ld_acquire(done + bb) == 0) {
+                        if (++spins > kSpinLimit) { timed_out = true; break; }
+                        __nanosleep(64);
+                    }
+                }
+            }
+            __threadfence_block();
+            g.sync();
+            // fixed point of the window: requirements only grow, and an
+            // in-window chain of length k settles after k + 1 passes
+            bool pending = m;
+            uint32_t cur = 0;
+            for (int it = 0; it < 40; it++) {
+                bool inwin = false, changed = false;
+                if (pending) {
+                    const uint32_t req = match_requirement(tok, blk_tok, tokdst, tags, src, ml, b,
+                                                           log2bs, n_tok, w, &inwin);
+                    changed = req != cur;
+                    cur = req;
+                }
+                if (changed) __stcg(tags + i, cur);
+                __threadfence_block();
+                g.sync();
+                pending = pending && inwin;
+                if (!g.ballot(changed) || !g.ballot(pending)) break;
+            }
+            if (m) mx = max(mx, cur);
+        }
+        if (g.ballot(timed_out) && g.lane == 0) atomicOr(err, kErrTimeout);
+        for (int o = 16; o; o >>= 1) mx = max(mx, g.shfl(mx, (g.lane + o) & 31));
+        __threadfence();
+        g.sync();
+        if (g.lane == 0) {
+            atomicMax(maxtag, mx);
+            st_release(done + b, 1u);
+        }
+    }
+}
+
+// Legality of given tags: tag >= requirement for every match, 0 for
+// literal-only tokens.
+__global__ void __launch_bounds__(256) k_tags_check(const uint4 *__restrict__ tok,
+                                                    const uint64_t *__restrict__ blk_tok,
+                                                    const uint32_t *__restrict__ tokdst,
+                                                    uint32_t *tags, uint32_t nb, uint32_t log2bs,
+                                                    uint64_t n_tok, uint32_t *maxtag, uint32_t *err) {
+    Group<32> g;
+    const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nb) return;
+    const uint64_t t0 = blk_tok[b], t1 = blk_tok[b + 1];
+    uint32_t mx = 0;
+    bool bad = false;
+    for (uint64_t w = t0; w < t1; w += 32) {
+        const uint64_t i = w + g.lane;
+        if (i < t1) {
+            const uint4 t = __ldg(tok + i);
+            const uint64_t sw = (uint64_t)t.z | ((uint64_t)t.w << 32);
+            const uint32_t tg = (uint32_t)(sw >> 40);
+            if (t.y) {
+                bool inwin = false;
+                const uint32_t req = match_requirement(tok, blk_tok, tokdst, tags, sw & kSrcMask, t.y, b,
+                                                       log2bs, n_tok, n_tok, &inwin);
+                if (req > tg) bad = true;
+            } else if (tg) {
+                bad = true;
+            }
+            mx = max(mx, tg);
+        }
+    }
+    for (int o = 16; o; o >>= 1) mx = max(mx, g.shfl(mx, (g.lane + o) & 31));
+    if (g.lane == 0) atomicMax(maxtag, mx);
+    if (g.ballot(bad) && g.lane == 0) atomicOr(err, kErrCorrupt);
+}
+
+__global__ void k_extract_tags(const uint4 *__restrict__ tok, uint32_t *tags, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        tags[i] = __ldg(tok + i).w >> 8;
+}
+
+__global__ void k_store_tags(uint4 *tok, const uint32_t *tags, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint4 t = tok[i];
+        t.w = (t.w & 0xffu) | (tags[i] << 8);
+        tok[i] = t;
+    }
+}
+
+// counts per (wave >= 1, block), wave-major
+__global__ void __launch_bounds__(256) k_wave_hist(const uint4 *__restrict__ tok,
+                                                   const uint64_t *__restrict__ blk_tok,
+                                                   uint32_t *cnt, uint32_t nb) {
+    const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;
+    for (uint64_t i = blk_tok[b] + lane; i < blk_tok[b + 1]; i += 32) {
+        const uint4 t = __ldg(tok + i);
+        const uint32_t tg = t.w >> 8;
+        if (t.y && tg) atomicAdd(cnt + (uint64_t)(tg - 1) * nb + b, 1u);
+    }
+}
+
+// slot of every deferred match: its (wave, block) segment base plus its
+// rank among that segment's matches in token order
+__global__ void __launch_bounds__(256) k_slots(const uint4 *__restrict__ tok,
+                                               const uint64_t *__restrict__ blk_tok, uint32_t *cursor,
+                                               uint32_t *slot, uint32_t nb) {
+    Group<32> g;
+    const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nb) return;
+    const uint64_t t0 = blk_tok[b], t1 = blk_tok[b + 1];
+    for (uint64_t w = t0; w < t1; w += 32) {
+        const uint64_t i = w + g.lane;
+        const bool v = i < t1;
+        uint4 t = v ? __ldg(tok + i) : make_uint4(0, 0, 0, 0);
+        const uint32_t tg = t.w >> 8;
+        const bool def = v && t.y && tg;
+        const unsigned long long key = def ? (unsigned long long)(tg - 1) * nb + b : ~0ULL;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        uint32_t basev = 0;
+        if (def && g.lane == leader) {
+            basev = cursor[key];
+            cursor[key] = basev + __popc(peers);
+        }
+        basev = __shfl_sync(0xffffffffu, basev, leader);
+        if (v) slot[i] = def ? basev + __popc(peers & g.lanemask_lt()) : 0xffffffffu;
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------- exclusive scan (u32)
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh, uint32_t *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t y = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        sh[lane] = y;
+    }
+    __syncthreads();
+    const uint32_t off = wid ? sh[wid - 1] : 0;
+    *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return off + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *in, uint64_t n,
+                                                              uint32_t *part) {
+    __shared__ uint32_t sh[32];
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t s = 0;
+    for (int k = 0; k < kScanItems; k++)
+        if (base + k < n) s += in[base + k];
+    uint32_t tot;
+    block_excl_scan(s, sh, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_parts(uint32_t *part, uint64_t np) {
+    __shared__ uint32_t sh[32];
+    uint32_t carry = 0;
+    for (uint64_t b = 0; b < np; b += kScanThreads) {
+        const uint64_t i = b + threadIdx.x;
+        const uint32_t v = i < np ? part[i] : 0;
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan(v, sh, &tot);
+        if (i < np) part[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) part[np] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t *io, uint64_t n,
+                                                             const uint32_t *part) {
+    __shared__ uint32_t sh[32];
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], s = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        v[k] = base + k < n ? io[base + k] : 0;
+        s += v[k];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(s, sh, &tot) + part[blockIdx.x];
+    for (int k = 0; k < kScanItems; k++) {
+        if (base + k < n) io[base + k] = ex;
+        ex += v[k];
+    }
+}
+
+__global__ void k_gather_starts(const uint32_t *base, uint64_t nb, uint32_t nw1, const uint32_t *total,
+                                uint64_t *starts) {
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w <= nw1; w += gridDim.x * blockDim.x)
+        starts[w] = w < nw1 ? base[(uint64_t)w * nb] : *total;
+}
+
+// ---------------------------------------------------------- host helpers
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+int cuda_rc(cudaError_t e) {
+    if (e == cudaSuccess) return ACLZ_OK;
+    return e == cudaErrorMemoryAllocation ? ACLZ_E_NOMEM : ACLZ_E_CUDA;
+}
+
+#define CK(x)                                \
+    do {                                     \
+        int _rc = cuda_rc(x);                \
+        if (_rc) { cleanup(); return _rc; }  \
+    } while (0)
+
+}  // namespace
+
+// Exclusive scan of n u32 in place (device), total to *d_total (device).
+// Temporary partials are allocated stream-ordered.
+static int device_excl_scan(uint32_t *d, uint64_t n, uint32_t *d_total, cudaStream_t st) {
+    const uint64_t ntile = (n + kScanTile - 1) / kScanTile;
+    uint32_t *part = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&part, sizeof(uint32_t) * (ntile + 1), st);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if (ntile) k_scan_reduce<<<(unsigned)ntile, kScanThreads, 0, st>>>(d, n, part);
+    k_scan_parts<<<1, kScanThreads, 0, st>>>(part, ntile);
+    if (ntile) k_scan_apply<<<(unsigned)ntile, kScanThreads, 0, st>>>(d, n, part);
+    cudaMemcpyAsync(d_total, part + ntile, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+    cudaFreeAsync(part, st);
+    return cuda_rc(cudaGetLastError());
+}
+
+extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_handle **out) {
+    if (!host_buf || !out) return ACLZ_E_INVAL;
+    *out = nullptr;
+    View v;
+    int rc = parse_container((const uint8_t *)host_buf, n, &v, true);
+    if (rc) return rc;
+    if (!is_pow2(v.block_size) || v.block_size < kMinBlock || v.block_size > kMaxBlock)
+        return ACLZ_E_UNSUPPORTED;
+    if (v.n_tokens >= 0xffffffffULL) return ACLZ_E_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    aclz_handle *h = new aclz_handle();
+    auto cleanup = [&]() { aclz_free(h); };
+    cudaGetDevice(&h->device);
+    h->total_len = v.total_len;
+    h->n_tokens = v.n_tokens;
+    h->n_literals = v.n_literals;
+    h->block_size = v.block_size;
+    h->log2_bs = log2u(v.block_size);
+    h->n_blocks = v.n_blocks;
+    h->flags = v.flags;
+    std::memcpy(h->mm, v.mm, 4);
+    const uint32_t nb = v.n_blocks;
+    const uint64_t nt = v.n_tokens;
+    // directory -> (nb + 1) offset arrays
+    std::vector<uint64_t> bt(nb + 1), bl(nb + 1);
+    for (uint32_t b = 0; b < nb; b++) {
+        bt[b] = rd64(v.dir + (uint64_t)kDirent * b);
+        bl[b] = rd64(v.dir + (uint64_t)kDirent * b + 8);
+    }
+    bt[nb] = nt;
+    bl[nb] = v.n_literals;
+    CK(cudaMalloc(&h->d_tok, kTok * (nt ? nt : 1)));
+    CK(cudaMalloc((void **)&h->d_lit, v.n_literals + 32));
+    CK(cudaMalloc((void **)&h->d_blk_tok, 8 * (nb + 1)));
+    CK(cudaMalloc((void **)&h->d_blk_lit, 8 * (nb + 1)));
+    CK(cudaMalloc((void **)&h->d_tokdst, 4 * (nt ? nt : 1)));
+    CK(cudaMalloc((void **)&h->d_slot, 4 * (nt ? nt : 1)));
+    CK(cudaMalloc((void **)&h->d_err, 64));
+    CK(cudaMemsetAsync(h->d_err, 0, 64, st));
+    CK(cudaMemsetAsync(h->d_lit + v.n_literals, 0, 32, st));
+    if (nt) CK(cudaMemcpyAsync(h->d_tok, v.tok, kTok * nt, cudaMemcpyHostToDevice, st));
+    if (v.n_literals) CK(cudaMemcpyAsync(h->d_lit, v.lit, v.n_literals, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->d_blk_tok, bt.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->d_blk_lit, bl.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, st));
+    if (nb == 0) {
+        h->n_waves = 0;
+        h->wave_start.assign(1, 0);
+        CK(cudaStreamSynchronize(st));
+        *out = h;
+        return ACLZ_OK;
+    }
+    // scratch words: [0] err (handle), work: maxtag, counter, total, first_bad
+    DevBuf work;
+    CK(cudaMalloc(&work.p, 64));
+    uint32_t *d_maxtag = (uint32_t *)work.p, *d_ctr = d_maxtag + 1, *d_total = d_maxtag + 2;
+    unsigned long long *d_first_bad = (unsigned long long *)((char *)work.p + 16);
+    CK(cudaMemsetAsync(work.p, 0, 16, st));
+    CK(cudaMemsetAsync(d_first_bad, 0xff, 8, st));
+    const unsigned wblocks = (nb + 7) / 8;  // 8 warps per CTA
+    const bool has_tags = (v.flags & kFlagWaves) != 0;
+    k_index_scan<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_blk_lit,
+                                           h->d_tokdst, nb, h->log2_bs, v.total_len, has_tags,
+                                           h->d_err, d_first_bad);
+    CK(cudaGetLastError());
+    uint32_t herr = 0;
+    CK(cudaMemcpyAsync(&herr, h->d_err, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) { cleanup(); return ACLZ_E_CORRUPT; }
+    // tags
+    DevBuf tags, done;
+    CK(cudaMalloc(&tags.p, 4 * (nt ? nt : 1)));
+    uint32_t *d_tags = (uint32_t *)tags.p;
+    if (has_tags) {
+        k_extract_tags<<<1024, 256, 0, st>>>((const uint4 *)h->d_tok, d_tags, nt);
+        k_tags_check<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_tokdst,
+                                               d_tags, nb, h->log2_bs, nt, d_maxtag, h->d_err);
+    } else {
+        CK(cudaMalloc(&done.p, 4 * nb));
+        CK(cudaMemsetAsync(done.p, 0, 4 * nb, st));
+        int dev_sms = 0;
+        cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tags_min, 256, 0);
+        unsigned grid = (unsigned)std::max(1, dev_sms * std::max(1, per_sm));
+        grid = std::min<unsigned>(grid, wblocks);
+        k_tags_min<<<grid, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_tokdst, d_tags,
+                                          (uint32_t *)done.p, d_ctr, nb, h->log2_bs, nt, d_maxtag,
+                                          h->d_err);
+        k_store_tags<<<1024, 256, 0, st>>>((uint4 *)h->d_tok, d_tags, nt);
+    }
+    CK(cudaGetLastError());
+    uint32_t hw[2] = {0, 0};
+    CK(cudaMemcpyAsync(&hw[0], d_maxtag, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hw[1], h->d_err, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hw[1] & kErrTimeout) { cleanup(); return ACLZ_E_TIMEOUT; }
+    if (hw[1]) { cleanup(); return ACLZ_E_CORRUPT; }
+    const uint32_t maxtag = hw[0];
+    if (maxtag > kMaxWave) { cleanup(); return ACLZ_E_UNSUPPORTED; }
+    if (has_tags && v.n_waves != maxtag + 1) { cleanup(); return ACLZ_E_CORRUPT; }
+    h->n_waves = maxtag + 1;
+    h->wave_start.assign(h->n_waves + 1, 0);
+    CK(cudaMemsetAsync(h->d_slot, 0xff, 4 * nt, st));
+    if (maxtag > 0) {
+        const uint64_t M = (uint64_t)maxtag * nb;
+        if (M > (1ULL << 31)) { cleanup(); return ACLZ_E_UNSUPPORTED; }
+        DevBuf cnt, starts;
+        CK(cudaMalloc(&cnt.p, 4 * M));
+        CK(cudaMalloc(&starts.p, 8 * (maxtag + 1)));
+        CK(cudaMemsetAsync(cnt.p, 0, 4 * M, st));
+        k_wave_hist<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, (uint32_t *)cnt.p, nb);
+        CK(cudaGetLastError());
+        rc = device_excl_scan((uint32_t *)cnt.p, M, d_total, st);
+        if (rc) { cleanup(); return rc; }
+        k_gather_starts<<<(maxtag + 256) / 256, 256, 0, st>>>((const uint32_t *)cnt.p, nb, maxtag, d_total,
+                                                            (uint64_t *)starts.p);
+        k_slots<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, (uint32_t *)cnt.p,
+                                          h->d_slot, nb);
+        CK(cudaGetLastError());
+        // wave_start[0] = wave_start[1] = 0: wave 0 has no triplets
+        CK(cudaMemcpyAsync(h->wave_start.data() + 1, starts.p, 8 * (maxtag + 1), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        h->n_deferred = h->wave_start[h->n_waves];
+        if (h->n_deferred) CK(cudaMalloc(&h->d_tri, 16 * h->n_deferred));
+    }
+    CK(cudaStreamSynchronize(st));
+    *out = h;
+    return ACLZ_OK;
+}
+
+extern "C" int aclz_free(aclz_handle *h) {
+    if (!h) return ACLZ_E_INVAL;
+    void *ps[] = {h->d_tok, h->d_lit, h->d_blk_tok, h->d_blk_lit, h->d_slot, h->d_tokdst,
+                  h->d_tri, h->d_err, h->d_items, h->d_prog, h->d_ctr};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    delete h;
+    return ACLZ_OK;
+}
+
+extern "C" int aclz_handle_info(const aclz_handle *h, aclz_info *out) {
+    if (!h || !out) return ACLZ_E_INVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->total_len = h->total_len;
+    out->n_tokens = h->n_tokens;
+    out->n_literals = h->n_literals;
+    out->n_deferred = h->n_deferred;
+    out->block_size = h->block_size;
+    out->n_blocks = h->n_blocks;
+    out->n_waves = h->n_waves;
+    out->flags = h->flags;
+    std::memcpy(out->min_match, h->mm, 4);
+    return ACLZ_OK;
+}
+
+extern "C" int aclz_wave_counts(const aclz_handle *h, uint64_t *counts, uint32_t cap) {
+    if (!h || (!counts && cap)) return ACLZ_E_INVAL;
+    for (uint32_t w = 0; w < cap && w < h->n_waves; w++)
+        counts[w] = h->wave_start[w + 1] - h->wave_start[w];
+    return ACLZ_OK;
+}
+
+extern "C" int aclz_tags(const aclz_handle *h, uint32_t *host_tags, uint64_t cap) {
+    if (!h || (!host_tags && cap)) return ACLZ_E_INVAL;
+    if (cap < h->n_tokens) return ACLZ_E_CAPACITY;
+    if (!h->n_tokens) return ACLZ_OK;
+    std::vector<uint32_t> raw(4 * h->n_tokens);
+    if (cudaMemcpy(raw.data(), h->d_tok, 16 * h->n_tokens, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ACLZ_E_CUDA;
+    for (uint64_t i = 0; i < h->n_tokens; i++) host_tags[i] = raw[4 * i + 3] >> 8;
+    return ACLZ_OK;
+}

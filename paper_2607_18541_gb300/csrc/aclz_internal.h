@@ -1,0 +1,79 @@
+// Internal declarations shared by the translation units of libaclz.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/aclz.h"
+
+namespace aclz {
+
+constexpr uint32_t kHdr = 64;
+constexpr uint32_t kDirent = 32;
+constexpr uint32_t kTok = 16;
+constexpr uint64_t kSrcMask = (1ULL << 40) - 1;
+constexpr uint32_t kMaxWave = (1u << 24) - 1;
+constexpr uint16_t kFlagWaves = 1;
+constexpr uint32_t kMinBlock = 64;
+constexpr uint32_t kMaxBlock = 1u << 24;
+
+// little-endian field access in host buffers
+inline uint16_t rd16(const uint8_t *p) { return (uint16_t)(p[0] | (p[1] << 8)); }
+inline uint32_t rd32(const uint8_t *p) {
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+inline uint64_t rd64(const uint8_t *p) { return (uint64_t)rd32(p) | ((uint64_t)rd32(p + 4) << 32); }
+inline void wr16(uint8_t *p, uint16_t v) { p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); }
+inline void wr32(uint8_t *p, uint32_t v) {
+    for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+inline void wr64(uint8_t *p, uint64_t v) {
+    for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+
+inline bool is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
+inline uint32_t log2u(uint64_t v) {
+    uint32_t k = 0;
+    while ((1ULL << k) < v) k++;
+    return k;
+}
+
+// Parsed header plus pointers into a host container.
+struct View {
+    uint64_t total_len = 0, n_tokens = 0, n_literals = 0;
+    uint32_t block_size = 0, n_blocks = 0, n_waves = 0;
+    uint16_t flags = 0;
+    uint8_t mm[4] = {0, 0, 0, 0};
+    const uint8_t *dir = nullptr, *tok = nullptr, *lit = nullptr;
+};
+
+// Header and directory checks on the host (O(n_blocks)); per-token checks
+// run on the device during upload.
+int parse_container(const uint8_t *c, uint64_t n, View *v, bool check_directory);
+
+}  // namespace aclz
+
+// Library handle: device copies of a container plus its decode index.
+struct aclz_handle {
+    int device = 0;
+    uint64_t total_len = 0, n_tokens = 0, n_literals = 0, n_deferred = 0;
+    uint32_t block_size = 0, log2_bs = 0, n_blocks = 0, n_waves = 0;
+    uint16_t flags = 0;
+    uint8_t mm[4] = {0, 0, 0, 0};
+    // device arrays (owned)
+    void *d_tok = nullptr;        // n_tokens x 16 B, tags filled in
+    uint8_t *d_lit = nullptr;     // n_literals + 32 zero bytes of padding
+    uint64_t *d_blk_tok = nullptr;  // n_blocks + 1 token offsets
+    uint64_t *d_blk_lit = nullptr;  // n_blocks + 1 literal offsets
+    uint32_t *d_slot = nullptr;   // per token: triplet slot of a deferred match, else ~0u
+    uint32_t *d_tokdst = nullptr; // per token: block-relative offset of its first byte
+    void *d_tri = nullptr;        // n_deferred x 16 B triplets (decode scratch)
+    uint32_t *d_err = nullptr;    // latched device status bits
+    std::vector<uint64_t> wave_start;  // n_waves + 1 entries into the triplet array
+    // persistent-mode schedule (built on first use)
+    void *d_items = nullptr;
+    uint64_t n_items = 0;
+    uint32_t *d_prog = nullptr;   // per block: next pending wave
+    uint32_t *d_ctr = nullptr;    // work counter
+};

@@ -1,0 +1,249 @@
+"""GPU parity of the decode path against the CPU oracle, through the C ABI.
+
+Every case compares the GPU output byte for byte with the oracle's
+sequential decode and checks the GPU FNV against the oracle FNV (integer
+work: the bar is bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_18541_gb300 import aclz, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    aclz.lib()  # raises if libaclz.so is missing: no fallback
+
+
+def gpu_decode(c, G=32, mode=aclz.ACLZ_MODE_WAVES, fnv=True):
+    s = torch.cuda.current_stream()
+    h = aclz.aclz_upload(c, s)
+    try:
+        info = aclz.aclz_handle_info(h)
+        out = torch.empty(max(16, info.total_len), dtype=torch.uint8, device="cuda")
+        aclz.aclz_decode_all(h, out, G=G, mode=mode, stream=s)
+        assert aclz.aclz_device_status(h, s) == aclz.ACLZ_OK
+        got = out[:info.total_len].cpu().numpy()
+        f = aclz.aclz_fnv(out, info.total_len, stream=s) if fnv else None
+        return got, f, h_info_dict(h)
+    finally:
+        aclz.aclz_free(h)
+
+
+def h_info_dict(h):
+    i = aclz.aclz_handle_info(h)
+    return dict(n_waves=i.n_waves, n_deferred=i.n_deferred, n_tokens=i.n_tokens)
+
+
+def check(c, G=32, mode=aclz.ACLZ_MODE_WAVES):
+    exp = oracle.decode(c)
+    got, f, info = gpu_decode(c, G, mode)
+    assert got.size == exp.size
+    if not np.array_equal(got, exp):
+        bad = np.nonzero(got != exp)[0]
+        raise AssertionError(f"{bad.size} bytes differ, first at {bad[0]} (G={G})")
+    assert f == oracle.fnv_chunked(exp)
+    return info
+
+
+# ------------------------------------------------------ workload configs
+
+def test_markov_4mib_base_thresholds_64k_blocks_g32():
+    """4 MiB order-2 Markov, 6/8/10/12, 64 KiB blocks, G = 32."""
+    x = synth.markov2(4 << 20, seed=synth.SEED_MARKOV)
+    c = oracle.encode(x, 1 << 16, oracle.PRESET_BASE)
+    info = check(c, 32)
+    assert info["n_waves"] >= 2
+    assert np.array_equal(oracle.decode(c), x)
+
+
+@pytest.mark.parametrize("G", [8, 16, 32])
+@pytest.mark.parametrize("L", [32, 64, 256, 1024])
+def test_copy_sweep_small(G, L):
+    sw = synth.copy_sweep((8 << 20) + 12345, 1 << 14, L, seed=100 + L)
+    check(oracle.pack_sweep(sw, tags=False), G)
+
+
+@pytest.mark.parametrize("bs", [1 << 12, 1 << 15, 1 << 17])
+def test_copy_sweep_block_sizes(bs):
+    sw = synth.copy_sweep(6 << 20, bs, 128, seed=bs)
+    check(oracle.pack_sweep(sw, tags=False), 32)
+
+
+@pytest.mark.parametrize("preset", [0, 1, 2])
+def test_fastq_presets(preset):
+    x = synth.fastq(3 << 20, seed=77)
+    mm = (oracle.PRESET_BASE, oracle.PRESET_TUNED, oracle.PRESET_PUSH)[preset]
+    check(oracle.encode(x, 1 << 14, mm), 32)
+
+
+def test_wordtext_and_product_encoder():
+    x = synth.wordtext(3 << 20, seed=5, chunk_bytes=1 << 20)
+    p = aclz.aclz_encode_params_default(aclz.ACLZ_PRESET_TUNED)
+    p.block_size = 1 << 16
+    c = aclz.aclz_encode(x, p)
+    got, f, _ = gpu_decode(c, 16)
+    assert np.array_equal(got, x)
+    assert f == oracle.fnv_chunked(x)
+
+
+# ------------------------------------------------------------ wave tags
+
+@pytest.mark.parametrize("kind", ["markov", "sweep", "fastq"])
+def test_gpu_tags_equal_oracle_minimal_tags(kind):
+    if kind == "markov":
+        c = oracle.encode(synth.markov2(2 << 20, seed=3), 1 << 12, oracle.PRESET_BASE)
+    elif kind == "sweep":
+        c = oracle.pack_sweep(synth.copy_sweep(4 << 20, 1 << 12, 48, seed=4))
+    else:
+        c = oracle.encode(synth.fastq(2 << 20, seed=5), 1 << 12, oracle.PRESET_BASE)
+    want, nw = oracle.min_tags(c)
+    s = torch.cuda.current_stream()
+    h = aclz.aclz_upload(oracle.strip_tags(c), s)  # GPU computes the tags
+    try:
+        got = aclz.aclz_tags(h)
+        assert aclz.aclz_handle_info(h).n_waves == nw
+    finally:
+        aclz.aclz_free(h)
+    assert np.array_equal(got, want)
+
+
+def test_given_and_nonminimal_tags_decode_identically():
+    x = synth.markov2(3 << 20, seed=8)
+    c = oracle.encode(x, 1 << 13, oracle.PRESET_BASE)       # minimal tags present
+    extra = np.random.default_rng(1).integers(0, 4, oracle.header(c).n_tokens).astype(np.uint32)
+    c2 = oracle.retag(c, extra)                               # legal, non-minimal
+    assert oracle.validate(c2) == 0
+    for cc in (c, c2, oracle.strip_tags(c)):
+        got, _, info = gpu_decode(cc, 32)
+        assert np.array_equal(got, x)
+
+
+# ------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("n", [0, 1, 15, 16, 17, 4095, 70000])
+def test_edge_sizes(n):
+    x = synth.markov2(max(n, 1), seed=11)[:n]
+    c = oracle.encode(x, 1 << 12, oracle.PRESET_BASE)
+    if n == 0:
+        s = torch.cuda.current_stream()
+        h = aclz.aclz_upload(c, s)
+        out = torch.empty(16, dtype=torch.uint8, device="cuda")
+        aclz.aclz_decode_all(h, out, stream=s)
+        assert aclz.aclz_device_status(h, s) == 0
+        aclz.aclz_free(h)
+        return
+    check(c, 8)
+
+
+def test_tiny_blocks_deep_waves_and_single_huge_block():
+    x = synth.markov2(200_000, seed=12)
+    check(oracle.encode(x, 64, (4, 4, 4, 4)), 32)          # 64-byte blocks, many waves
+    check(oracle.encode(x, 1 << 24, oracle.PRESET_BASE), 16)  # one 16 MiB block
+    z = np.zeros(300_000, dtype=np.uint8)                     # constant run: doubling chain
+    check(oracle.encode(z, 1 << 12, oracle.PRESET_BASE, chain_depth=oracle.UNLIMITED_DEPTH), 32)
+    r = np.frombuffer(np.random.default_rng(0).bytes(100_000), dtype=np.uint8)  # literal only
+    check(oracle.encode(r, 1 << 12, oracle.PRESET_BASE), 32)
+
+
+def test_misaligned_sources_and_in_block_chains():
+    # matches at every alignment of src and dst mod 16, chains inside a block
+    rng = np.random.default_rng(3)
+    blk, ll, ml, sr, lits = [], [], [], [], bytearray()
+    total, bs = 0, 1 << 12
+    for b in range(64):
+        pos, cnt = b * bs, 0
+        end = pos + bs
+        while pos < end:
+            lit = int(rng.integers(0, 20))
+            m = int(rng.integers(1, 80))
+            if pos + lit + m <= end and pos + lit >= m:
+                src = int(rng.integers(max(0, pos + lit - 3000), pos + lit - m + 1))
+                ll.append(lit); ml.append(m); sr.append(src)
+                lits += rng.bytes(lit)
+                pos += lit + m
+            else:
+                ll.append(end - pos); ml.append(0); sr.append(0)
+                lits += rng.bytes(end - pos)
+                pos = end
+            cnt += 1
+        blk.append(cnt)
+        total = end
+    c = oracle.pack(total, bs, blk, ll, ml, sr, bytes(lits), tags=False)
+    for G in (8, 16, 32):
+        check(c, G)
+
+
+# ------------------------------------------------------------ corruption
+
+def test_corrupt_containers_are_rejected_on_upload():
+    x = synth.markov2(1 << 20, seed=13)
+    c = oracle.encode(x, 1 << 14, oracle.PRESET_BASE)
+    h = oracle.header(c)
+    t0 = 64 + 32 * h.n_blocks
+    _, ll, ml, src, wave, _ = oracle.tokens(c)
+    mi = int(np.nonzero(wave)[0][5])
+    bad = []
+    b = c.copy(); b[t0 + 16 * mi + 4] ^= 2; bad.append(b)               # length sum
+    b = c.copy()
+    b[t0 + 16 * mi + 8:t0 + 16 * mi + 13] = np.frombuffer((h.total_len - 1).to_bytes(5, "little"), np.uint8)
+    bad.append(b)                                                        # src after dst
+    b = c.copy()                                                         # illegal (too small) tag
+    sw64 = b[t0 + 16 * mi + 8:t0 + 16 * mi + 16].view(np.uint64)
+    sw64[0] = np.uint64(int(sw64[0]) - (1 << 40))
+    bad.append(b)
+    s = torch.cuda.current_stream()
+    for b in bad:
+        assert oracle.validate(b) < 0
+        with pytest.raises(aclz.AclzError) as e:
+            hh = aclz.aclz_upload(b, s)
+            aclz.aclz_free(hh)
+        assert e.value.code == aclz.ACLZ_E_CORRUPT
+
+
+def test_output_buffer_checks():
+    c = oracle.encode(synth.markov2(10000, seed=1), 1 << 12, oracle.PRESET_BASE)
+    s = torch.cuda.current_stream()
+    h = aclz.aclz_upload(c, s)
+    try:
+        small = torch.empty(100, dtype=torch.uint8, device="cuda")
+        with pytest.raises(aclz.AclzError) as e:
+            aclz.aclz_decode_all(h, small, stream=s)
+        assert e.value.code == aclz.ACLZ_E_CAPACITY
+        buf = torch.empty(20000, dtype=torch.uint8, device="cuda")
+        with pytest.raises(aclz.AclzError) as e:
+            aclz.aclz_decode_all(h, buf.data_ptr() + 1, cap=19999, stream=s)
+        assert e.value.code == aclz.ACLZ_E_INVAL
+        with pytest.raises(aclz.AclzError):
+            aclz.aclz_decode_all(h, buf, G=12, stream=s)
+    finally:
+        aclz.aclz_free(h)
+
+
+# ------------------------------------------------------------------- FNV
+
+@pytest.mark.parametrize("n", [0, 1, 65535, 65536, 65537, (3 << 20) + 5])
+def test_fnv_matches_oracle(n):
+    x = np.frombuffer(np.random.default_rng(n).bytes(max(n, 1)), dtype=np.uint8)[:n].copy()
+    t = torch.from_numpy(x if n else np.zeros(1, np.uint8)).cuda()
+    assert aclz.aclz_fnv(t, n) == oracle.fnv_chunked(x)
+
+
+# ------------------------------------------------------- full-size case
+
+@pytest.mark.parametrize("L", [1024, 32])
+def test_copy_sweep_1gib_full_size(L):
+    """1 GiB copy sweep in the benchmark's launch configuration (G = 32,
+    32 KiB blocks): every output byte against the oracle, and FNV."""
+    sw = synth.copy_sweep(1 << 30, 1 << 15, L, seed=synth.SEED_COPY + L)
+    c = aclz.aclz_pack(sw.total, sw.block_size, (4, 4, 4, 4), sw.blk_ntok, sw.lit_len, sw.match_len,
+                       sw.src, sw.literals)
+    exp = oracle.decode(oracle.pack_sweep(sw, tags=False))
+    got, f, info = gpu_decode(c, 32)
+    assert np.array_equal(got, exp)
+    assert f == oracle.fnv_chunked(exp)
