@@ -169,6 +169,19 @@ int aclz_device_status(aclz_handle *h, void *stream);
  * of 8 bytes per chunk. */
 int aclz_fnv(const void *d_buf, uint64_t n, uint64_t *out_hash, void *stream);
 
+/* Same hash as aclz_fnv, for callers that must not allocate device memory
+ * during the call (a nearly full device, memory owned by an arena or pool
+ * manager, a latency-critical path that must stay out of the allocator).
+ * The paper has no counterpart; this is a library convenience.  The chunk
+ * hashes go to one fixed 512 KiB array inside the library, so n is limited
+ * to 4 GiB (65536 chunks of 64 KiB): larger n returns ACLZ_E_CAPACITY.
+ * The first call on each device looks up that array's device address (make
+ * that first call before any stream capture).  All calls share the array:
+ * calls that overlap on the GPU race and may return wrong hashes.
+ * Synchronous: *out_hash holds the result on return.  No cudaMalloc or
+ * cudaFree is made. */
+int aclz_fnv_noalloc(const void *d_buf, uint64_t n, uint64_t *out_hash, void *stream);
+
 const char *aclz_strerror(int code);
 
 #ifdef __cplusplus

@@ -80,7 +80,9 @@ _SIGS = [
     ("aclz_fnv", _I, [_VP, _U64, _U64P, _VP]),
     ("aclz_strerror", ctypes.c_char_p, [_I]),
 ]
-OPTIONAL_SIGS: list = []  # entry points added by later modules register here
+OPTIONAL_SIGS: list = [  # entry points added by later modules register here
+    ("aclz_fnv_noalloc", _I, [_VP, _U64, _U64P, _VP]),
+]
 
 
 def lib() -> ctypes.CDLL:
@@ -244,4 +246,14 @@ def aclz_fnv(d_buf, n: int | None = None, stream=None) -> int:
         n = int(d_buf.numel() * d_buf.element_size())
     out = ctypes.c_uint64(0)
     _ck(lib().aclz_fnv(_dptr(d_buf), n, ctypes.byref(out), _stream(stream)), "aclz_fnv")
+    return int(out.value)
+
+
+def aclz_fnv_noalloc(d_buf, n: int | None = None, stream=None) -> int:
+    """aclz_fnv without device allocation (fixed 4 GiB limit, calls must not
+    overlap on the GPU); see include/aclz.h."""
+    if n is None:
+        n = int(d_buf.numel() * d_buf.element_size())
+    out = ctypes.c_uint64(0)
+    _ck(lib().aclz_fnv_noalloc(_dptr(d_buf), n, ctypes.byref(out), _stream(stream)), "aclz_fnv_noalloc")
     return int(out.value)
