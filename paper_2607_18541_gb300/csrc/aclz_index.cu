@@ -288,6 +288,40 @@ __global__ void __launch_bounds__(256) k_slots(const uint4 *__restrict__ tok,
     }
 }
 
+// flag[k] = 1 when (wave, block) segment k is non-empty; base is the
+// exclusive scan of the segment counts, *total its sum
+__global__ void k_seg_flags(const uint32_t *base, uint64_t M, const uint32_t *total, uint32_t *flag) {
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < M;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t nxt = k + 1 < M ? base[k + 1] : *total;
+        flag[k] = nxt > base[k] ? 1u : 0u;
+    }
+}
+
+// Work items of the persistent decode, wave-major: item b = wave 0 of
+// block b; then one item per non-empty (wave, block) segment, placed by the
+// compaction scan pos.  next[i] = the block's next non-empty wave after
+// item i (0xffffffff when none).
+__global__ void k_items_build(const uint32_t *base, const uint32_t *pos, const uint32_t *total,
+                              uint32_t nb, uint32_t nw1, uint4 *items, uint32_t *next) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const uint64_t M = (uint64_t)nw1 * nb;
+    items[b] = make_uint4(b, 0u, 0u, 0u);
+    uint64_t prev = b;
+    for (uint32_t w = 1; w <= nw1; w++) {
+        const uint64_t k = (uint64_t)(w - 1) * nb + b;
+        const uint32_t nxt = k + 1 < M ? base[k + 1] : *total;
+        const uint32_t c = nxt - base[k];
+        if (!c) continue;
+        const uint64_t idx = nb + pos[k];
+        items[idx] = make_uint4(b, w, base[k], c);
+        next[prev] = w;
+        prev = idx;
+    }
+    next[prev] = 0xffffffffu;
+}
+
 // ------------------------------------------------- exclusive scan (u32)
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
@@ -518,6 +552,27 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
         if (rc) { cleanup(); return rc; }
         k_gather_starts<<<(maxtag + 256) / 256, 256, 0, st>>>((const uint32_t *)cnt.p, nb, maxtag, d_total,
                                                             (uint64_t *)starts.p);
+        // persistent-mode items from the segment bases (before k_slots turns
+        // the bases into cursors)
+        {
+            DevBuf flag;
+            CK(cudaMalloc(&flag.p, 4 * M));
+            k_seg_flags<<<1024, 256, 0, st>>>((const uint32_t *)cnt.p, M, d_total, (uint32_t *)flag.p);
+            uint32_t *d_nseg = d_total + 1;
+            rc = device_excl_scan((uint32_t *)flag.p, M, d_nseg, st);
+            if (rc) { cleanup(); return rc; }
+            uint32_t nseg = 0;
+            CK(cudaMemcpyAsync(&nseg, d_nseg, 4, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            h->n_items = (uint64_t)nb + nseg;
+            CK(cudaMalloc(&h->d_items, 16 * h->n_items));
+            CK(cudaMalloc((void **)&h->d_next, 4 * h->n_items));
+            k_items_build<<<(nb + 255) / 256, 256, 0, st>>>((const uint32_t *)cnt.p, (const uint32_t *)flag.p,
+                                                           d_total, nb, maxtag, (uint4 *)h->d_items,
+                                                           h->d_next);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(st));
+        }
         k_slots<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, (uint32_t *)cnt.p,
                                           h->d_slot, nb);
         CK(cudaGetLastError());
@@ -527,6 +582,16 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
         h->n_deferred = h->wave_start[h->n_waves];
         if (h->n_deferred) CK(cudaMalloc(&h->d_tri, 16 * h->n_deferred));
     }
+    if (!h->d_items) {
+        h->n_items = nb;
+        CK(cudaMalloc(&h->d_items, 16 * h->n_items));
+        CK(cudaMalloc((void **)&h->d_next, 4 * h->n_items));
+        std::vector<uint32_t> it(4 * (size_t)nb), nx(nb, 0xffffffffu);
+        for (uint32_t b = 0; b < nb; b++) { it[4 * b] = b; it[4 * b + 1] = it[4 * b + 2] = it[4 * b + 3] = 0; }
+        CK(cudaMemcpyAsync(h->d_items, it.data(), 16 * (size_t)nb, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(h->d_next, nx.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMalloc((void **)&h->d_prog, 4 * (size_t)nb));
     CK(cudaStreamSynchronize(st));
     *out = h;
     return ACLZ_OK;
@@ -535,7 +600,7 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
 extern "C" int aclz_free(aclz_handle *h) {
     if (!h) return ACLZ_E_INVAL;
     void *ps[] = {h->d_tok, h->d_lit, h->d_blk_tok, h->d_blk_lit, h->d_slot, h->d_tokdst,
-                  h->d_tri, h->d_err, h->d_items, h->d_prog, h->d_ctr};
+                  h->d_tri, h->d_err, h->d_items, h->d_next, h->d_prog, h->d_ctr};
     for (void *p : ps)
         if (p) cudaFree(p);
     delete h;

@@ -71,9 +71,12 @@ struct aclz_handle {
     void *d_tri = nullptr;        // n_deferred x 16 B triplets (decode scratch)
     uint32_t *d_err = nullptr;    // latched device status bits
     std::vector<uint64_t> wave_start;  // n_waves + 1 entries into the triplet array
-    // persistent-mode schedule (built on first use)
+    // persistent-mode schedule: wave-major items, item i = {block, wave,
+    // triplet offset, triplet count}; items [0, n_blocks) are the wave-0
+    // block decodes, then one item per non-empty (wave, block) segment
     void *d_items = nullptr;
+    uint32_t *d_next = nullptr;   // per item: the block's next non-empty wave
     uint64_t n_items = 0;
-    uint32_t *d_prog = nullptr;   // per block: next pending wave
-    uint32_t *d_ctr = nullptr;    // work counter
+    uint32_t *d_prog = nullptr;   // per block: waves below this value are final
+    uint32_t *d_ctr = nullptr;    // reserved
 };

@@ -40,14 +40,20 @@ def h_info_dict(h):
     return dict(n_waves=i.n_waves, n_deferred=i.n_deferred, n_tokens=i.n_tokens)
 
 
-def check(c, G=32, mode=aclz.ACLZ_MODE_WAVES):
+MODES = (aclz.ACLZ_MODE_WAVES, aclz.ACLZ_MODE_PERSISTENT)
+
+
+def check(c, G=32, modes=MODES):
+    """Decode c in each mode; byte compare and FNV against the oracle."""
     exp = oracle.decode(c)
-    got, f, info = gpu_decode(c, G, mode)
-    assert got.size == exp.size
-    if not np.array_equal(got, exp):
-        bad = np.nonzero(got != exp)[0]
-        raise AssertionError(f"{bad.size} bytes differ, first at {bad[0]} (G={G})")
-    assert f == oracle.fnv_chunked(exp)
+    fe = oracle.fnv_chunked(exp)
+    for mode in modes:
+        got, f, info = gpu_decode(c, G, mode)
+        assert got.size == exp.size
+        if not np.array_equal(got, exp):
+            bad = np.nonzero(got != exp)[0]
+            raise AssertionError(f"{bad.size} bytes differ, first at {bad[0]} (G={G}, mode={mode})")
+        assert f == fe
     return info
 
 
@@ -87,9 +93,10 @@ def test_wordtext_and_product_encoder():
     p = aclz.aclz_encode_params_default(aclz.ACLZ_PRESET_TUNED)
     p.block_size = 1 << 16
     c = aclz.aclz_encode(x, p)
-    got, f, _ = gpu_decode(c, 16)
-    assert np.array_equal(got, x)
-    assert f == oracle.fnv_chunked(x)
+    for mode in MODES:
+        got, f, _ = gpu_decode(c, 16, mode)
+        assert np.array_equal(got, x)
+        assert f == oracle.fnv_chunked(x)
 
 
 # ------------------------------------------------------------ wave tags
@@ -120,8 +127,9 @@ def test_given_and_nonminimal_tags_decode_identically():
     c2 = oracle.retag(c, extra)                               # legal, non-minimal
     assert oracle.validate(c2) == 0
     for cc in (c, c2, oracle.strip_tags(c)):
-        got, _, info = gpu_decode(cc, 32)
-        assert np.array_equal(got, x)
+        for mode in MODES:
+            got, _, info = gpu_decode(cc, 32, mode)
+            assert np.array_equal(got, x)
 
 
 # ------------------------------------------------------------ edge cases
@@ -244,6 +252,8 @@ def test_copy_sweep_1gib_full_size(L):
     c = aclz.aclz_pack(sw.total, sw.block_size, (4, 4, 4, 4), sw.blk_ntok, sw.lit_len, sw.match_len,
                        sw.src, sw.literals)
     exp = oracle.decode(oracle.pack_sweep(sw, tags=False))
-    got, f, info = gpu_decode(c, 32)
-    assert np.array_equal(got, exp)
-    assert f == oracle.fnv_chunked(exp)
+    fe = oracle.fnv_chunked(exp)
+    for mode in MODES:
+        got, f, info = gpu_decode(c, 32, mode)
+        assert np.array_equal(got, exp)
+        assert f == fe
