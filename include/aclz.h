@@ -143,19 +143,29 @@ int aclz_wave_counts(const aclz_handle *h, uint64_t *counts, uint32_t cap);
  * to host memory. */
 int aclz_tags(const aclz_handle *h, uint32_t *host_tags, uint64_t cap);
 
+/* Regroup the persistent schedule: consecutive (block, wave) segments are
+ * packed into work ranges of about range_bytes of deferred matches (upload
+ * picks 16 KiB).  Synchronizes the stream.  Used by the autotuner. */
+int aclz_set_range_bytes(aclz_handle *h, uint32_t range_bytes, void *stream);
+
 typedef struct aclz_decode_cfg {
     uint32_t G;           /* cooperating lanes per group: 8, 16 or 32 */
     uint32_t mode;        /* ACLZ_MODE_WAVES or ACLZ_MODE_PERSISTENT */
-    uint32_t ctas_per_sm; /* persistent mode: resident CTAs per SM (0 = max) */
-    uint32_t flags;       /* reserved, 0 */
+    uint32_t ctas_per_sm; /* persistent mode: resident CTAs per SM (0 = most) */
+    uint32_t flags;       /* ACLZ_FLAG_* */
 } aclz_decode_cfg;
 
-#define ACLZ_MODE_WAVES 0      /* one kernel per wave */
-#define ACLZ_MODE_PERSISTENT 1 /* one launch, bounded per-block waits */
+#define ACLZ_MODE_WAVES 0      /* wave 0, then one kernel per wave */
+#define ACLZ_MODE_PERSISTENT 1 /* wave 0, then one launch with bounded per-block waits */
+#define ACLZ_FLAG_STAGED 1u    /* persistent: stage long matches through shared memory (TMA) */
+#define ACLZ_FLAG_REGISTERS 2u /* persistent: copy through registers only */
 
 /* Decode the whole stream into d_out (cap >= total_len bytes, 16-byte
  * aligned).  Enqueues on stream; capturable in a CUDA graph (no allocation,
- * no synchronization).  cfg NULL = {32, ACLZ_MODE_WAVES, 0, 0}. */
+ * no synchronization).  cfg NULL = {32, ACLZ_MODE_PERSISTENT, 0, 0}; the
+ * persistent mode stages long matches through shared memory when the
+ * deferred matches average at least 192 bytes, unless a flag forces one
+ * copy path. */
 int aclz_decode_all(aclz_handle *h, void *d_out, uint64_t cap, const aclz_decode_cfg *cfg,
                     void *stream);
 
@@ -183,6 +193,10 @@ int aclz_fnv(const void *d_buf, uint64_t n, uint64_t *out_hash, void *stream);
 int aclz_fnv_noalloc(const void *d_buf, uint64_t n, uint64_t *out_hash, void *stream);
 
 const char *aclz_strerror(int code);
+
+/* The cudaError_t value behind the most recent ACLZ_E_CUDA (0 if none),
+ * process-wide. */
+int aclz_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

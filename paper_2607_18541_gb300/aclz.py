@@ -30,11 +30,14 @@ ACLZ_E_DEVICE = -7
 ACLZ_E_UNSUPPORTED = -8
 ACLZ_PRESET_BASE, ACLZ_PRESET_TUNED, ACLZ_PRESET_PUSH = 0, 1, 2
 ACLZ_MODE_WAVES, ACLZ_MODE_PERSISTENT = 0, 1
+ACLZ_FLAG_STAGED, ACLZ_FLAG_REGISTERS = 1, 2
 
 
 class AclzError(RuntimeError):
     def __init__(self, code: int, what: str):
         msg = aclz_strerror(code) if _lib is not None else str(code)
+        if code == ACLZ_E_CUDA and _lib is not None:
+            msg += f" (cudaError {_lib.aclz_last_cuda_error()})"
         super().__init__(f"{what}: {msg} ({code})")
         self.code = code
 
@@ -75,10 +78,12 @@ _SIGS = [
     ("aclz_handle_info", _I, [_VP, ctypes.POINTER(aclz_info)]),
     ("aclz_wave_counts", _I, [_VP, _U64P, _U32]),
     ("aclz_tags", _I, [_VP, _U32P, _U64]),
+    ("aclz_set_range_bytes", _I, [_VP, _U32, _VP]),
     ("aclz_decode_all", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP]),
     ("aclz_device_status", _I, [_VP, _VP]),
     ("aclz_fnv", _I, [_VP, _U64, _U64P, _VP]),
     ("aclz_strerror", ctypes.c_char_p, [_I]),
+    ("aclz_last_cuda_error", _I, []),
 ]
 OPTIONAL_SIGS: list = [  # entry points added by later modules register here
     ("aclz_fnv_noalloc", _I, [_VP, _U64, _U64P, _VP]),
@@ -229,11 +234,16 @@ def aclz_tags(h: int) -> np.ndarray:
     return out[:nt]
 
 
-def aclz_decode_all(h: int, d_out, cap: int | None = None, G: int = 32, mode: int = ACLZ_MODE_WAVES,
-                    ctas_per_sm: int = 0, stream=None) -> None:
+def aclz_set_range_bytes(h: int, range_bytes: int, stream=None) -> None:
+    _ck(lib().aclz_set_range_bytes(h, range_bytes, _stream(stream)), "aclz_set_range_bytes")
+
+
+def aclz_decode_all(h: int, d_out, cap: int | None = None, G: int = 32,
+                    mode: int = ACLZ_MODE_PERSISTENT, ctas_per_sm: int = 0, flags: int = 0,
+                    stream=None) -> None:
     if cap is None:
         cap = int(d_out.numel() * d_out.element_size())
-    cfg = aclz_decode_cfg(G, mode, ctas_per_sm, 0)
+    cfg = aclz_decode_cfg(G, mode, ctas_per_sm, flags)
     _ck(lib().aclz_decode_all(h, _dptr(d_out), cap, ctypes.byref(cfg), _stream(stream)), "aclz_decode_all")
 
 

@@ -6,16 +6,22 @@
 // source is already final in block order (tag 0), and writes each deferred
 // match as a (dst, src, len) triplet into its wave's worklist.
 //
-// Waves w >= 1 (k_wave_copy): the worklist of wave w holds the matches
-// whose sources became final in earlier waves (the wavefront of Sec. I),
-// in block order.  Groups take contiguous ranges cut at block boundaries,
-// and only matches of one block whose source overlaps an earlier match of
-// the same block in the same pass are serialised.
+// Waves w >= 1 hold the matches whose sources become final only in earlier
+// waves (the wavefront of Sec. I), block-ordered within each wave.  Two
+// schedules run them:
+//  - ACLZ_MODE_WAVES: one kernel per wave (k_wave_copy), kernel boundaries
+//    as the wave barrier;
+//  - ACLZ_MODE_PERSISTENT: one cooperative launch (k_ranges) over ranges of
+//    consecutive (block, wave) segments in wave-major order, with bounded
+//    waits on per-block completed-wave bits instead of wave barriers, so a
+//    match is copied as soon as the blocks it reads have finished the waves
+//    below its own.
 //
-// All copies go through group_copy: every lane owns one aligned 16-byte
-// output chunk, so short matches from several tokens share one pass
-// instead of leaving most of the group idle (the work-granularity
-// mechanism of Sec. III-C).
+// All copies are 16-byte vectorised with every lane owning aligned output
+// chunks, so short matches from several tokens share one pass instead of
+// leaving most of the group idle (the work-granularity mechanism of
+// Sec. III-C); long matches in the persistent schedule are staged through
+// shared memory by TMA bulk copies (cp.async.bulk + mbarrier).
 #include <algorithm>
 #include <cstring>
 
@@ -27,41 +33,53 @@ using namespace aclz;
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;
+constexpr int kUnrollWave = 2;   // chunks per lane per round in the wave-0 pass
+constexpr int kUnrollCopy = 4;   // chunks per lane per round in match copies
+// staged (TMA) copies: jobs of at least kTmaMin bytes, pieces of <= kPiece
+constexpr uint32_t kTmaMin = 192;
+constexpr uint32_t kPiece = 2048;
+constexpr uint32_t kSmemPerSm = 220u * 1024u;  // stage memory shared by the CTAs of one SM
 
 __device__ __forceinline__ uint64_t tri_dst(const uint4 t) { return (uint64_t)t.x | ((uint64_t)(t.y & 0xffu) << 32); }
 __device__ __forceinline__ uint64_t tri_src(const uint4 t) { return (uint64_t)t.z | ((uint64_t)(t.w & 0xffu) << 32); }
 __device__ __forceinline__ uint32_t tri_len(const uint4 t) { return t.w >> 8; }
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
-constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits: ~0.3-1 s at most
+constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits: about a second at most
 
-// Spin (bounded) until *p >= v; returns false when the limit ran out or
-// when another group already gave up (err has kErrTimeout), so one stuck
-// wait ends the whole launch within about a second.
-__device__ __forceinline__ bool wait_at_least(const uint32_t *p, uint32_t v, uint32_t *err) {
-    uint32_t spins = 0;
-    while (ld_acquire(p) < v) {
-        if (++spins > kSpinLimit) {
-            atomicOr(err, kErrTimeout);
-            return false;
+// A bounded wait gives up when the limit runs out or when another group
+// already gave up (err has kErrTimeout), so one stuck wait ends the whole
+// launch within about a second.
+
+// Spin (bounded) until every wave below w of one block is done: its done
+// bits (ww 64-bit words, empty waves preset) are all set below bit w.
+__device__ __forceinline__ bool wait_waves_below(const unsigned long long *done, uint32_t w, uint32_t *err) {
+    for (uint32_t k = 0; k * 64 < w; k++) {
+        const uint32_t nbits = w - k * 64;
+        const unsigned long long want = nbits >= 64 ? ~0ULL : ((1ULL << nbits) - 1ULL);
+        uint32_t spins = 0;
+        while ((ld_acquire64(done + k) & want) != want) {
+            if (++spins > kSpinLimit) {
+                atomicOr(err, kErrTimeout);
+                return false;
+            }
+            if ((spins & 255) == 0 && (*(volatile uint32_t *)err & kErrTimeout)) return false;
+            __nanosleep(spins < 64 ? 32 : 256);
         }
-        if ((spins & 255) == 0 && (*(volatile uint32_t *)err & kErrTimeout)) return false;
-        __nanosleep(spins < 64 ? 32 : 256);
     }
     return true;
 }
 
+// ------------------------------------------------------------- wave 0
+
 // Wave 0 of one block: scan, literal runs, in-order (tag 0) matches, and
-// the deferred matches' triplets.
+// the deferred matches' triplets.  The next window's tokens are loaded
+// while the current window is copied.
 template <int G>
 __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const uint4 *__restrict__ tok,
                                             const uint8_t *__restrict__ lit,
@@ -72,10 +90,12 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
     const uint64_t t0 = blk_tok[b], t1 = blk_tok[b + 1];
     uint64_t lbase = blk_lit[b];
     uint64_t pos = (uint64_t)b << log2bs;
+    uint4 nt = t0 + g.lane < t1 ? __ldg(tok + t0 + g.lane) : make_uint4(0, 0, 0, 0);
     for (uint64_t w = t0; w < t1; w += G) {
         const uint64_t i = w + g.lane;
         const bool v = i < t1;
-        const uint4 t = v ? __ldg(tok + i) : make_uint4(0, 0, 0, 0);
+        const uint4 t = v ? nt : make_uint4(0, 0, 0, 0);
+        if (w + G + g.lane < t1) nt = __ldg(tok + w + G + g.lane);
         const uint32_t ll = t.x, ml = t.y;
         const uint32_t tag = t.w >> 8;
         const uint64_t src = (uint64_t)t.z | ((uint64_t)(t.w & 0xffu) << 32);
@@ -83,15 +103,14 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
         const uint32_t lincl = g.scan_incl(ll);
         const uint64_t dl = pos + incl - (ll + ml);
         const uint64_t dm = dl + ll;
-        const uint8_t *ls = lit + (lbase + lincl - ll);
-        // literal runs: sources in the literal array, always independent
-        group_copy<G, kUnroll>(g, out, dl, ls, ll);
         // deferred matches go to their wave's worklist
         if (v && ml && tag) {
             const uint32_t sl = __ldg(slot + i);
             __stcg(tri + sl, make_uint4((uint32_t)dm, (uint32_t)(dm >> 32), (uint32_t)src,
                                         (uint32_t)(src >> 32) | (ml << 8)));
         }
+        // literal runs: sources in the literal array, always independent
+        group_copy<G, kUnrollWave>(g, out, dl, lit + (lbase + lincl - ll), ll);
         g.sync();
         // in-order matches, batched so no batch reads what it writes
         const bool m0 = v && ml && tag == 0;
@@ -104,7 +123,7 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
             const unsigned lim = dmask & (0u - dmask);
             const unsigned batch = lim ? (rem & (lim - 1u)) : rem;
             const bool mine = (batch >> g.lane) & 1u;
-            group_copy<G, kUnroll>(g, out, dm, out + src, mine ? ml : 0u);
+            group_copy<G, kUnrollWave>(g, out, dm, out + src, mine ? ml : 0u);
             g.sync();
             rem &= ~batch;
         }
@@ -113,92 +132,128 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
     }
 }
 
+// Wave 0 of every block, one group per block.  With done non-null (the
+// persistent schedule follows), each block's done bits start as its empty
+// waves plus wave 0.
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_wave0(const uint4 *__restrict__ tok,
-                                                    const uint8_t *__restrict__ lit,
-                                                    const uint64_t *__restrict__ blk_tok,
-                                                    const uint64_t *__restrict__ blk_lit,
-                                                    const uint32_t *__restrict__ slot,
-                                                    uint4 *__restrict__ tri, uint8_t *out, uint32_t nb,
-                                                    uint32_t log2bs) {
+__global__ void __launch_bounds__(kThreads, 3) k_wave0(const uint4 *__restrict__ tok,
+                                                       const uint8_t *__restrict__ lit,
+                                                       const uint64_t *__restrict__ blk_tok,
+                                                       const uint64_t *__restrict__ blk_lit,
+                                                       const uint32_t *__restrict__ slot,
+                                                       uint4 *__restrict__ tri, uint8_t *out, uint32_t nb,
+                                                       uint32_t log2bs, const uint64_t *__restrict__ pending,
+                                                       uint64_t *done, uint32_t ww) {
     Group<G> g;
     const uint32_t b = (uint32_t)((blockIdx.x * (uint64_t)kThreads + threadIdx.x) / G);
     if (b >= nb) return;
     block_wave0<G>(g, b, tok, lit, blk_tok, blk_lit, slot, tri, out, log2bs);
+    if (done)
+        for (uint32_t k = g.lane; k < ww; k += G)
+            done[(uint64_t)b * ww + k] = ~__ldg(pending + (uint64_t)b * ww + k) | (k == 0 ? 1ULL : 0ULL);
 }
 
-// One block's segment of wave w >= 1 inside the persistent decode: wait
-// until every source block has finished the waves below w, then copy with
-// same-block dependencies serialised.
-template <int G>
-__device__ __forceinline__ bool block_segment(const Group<G> &g, uint32_t b, uint32_t w,
-                                              const uint4 *tri, uint64_t n, const uint32_t *prog,
-                                              uint8_t *out, uint32_t log2bs, uint32_t *err) {
-    bool ok = true;
-    for (uint64_t cur = 0; cur < n; cur += G) {
-        const uint64_t i = cur + g.lane;
-        const bool v = i < n;
-        const uint4 t = v ? __ldcg(tri + i) : make_uint4(0, 0, 0, 0);
-        const uint64_t d = tri_dst(t), sr = tri_src(t);
-        const uint32_t len = v ? tri_len(t) : 0u;
-        if (v) {
-            const uint64_t b0 = sr >> log2bs, b1 = (sr + len - 1) >> log2bs;
-            for (uint64_t bb = b0; bb <= b1; bb++)
-                if (bb != b && !wait_at_least(prog + bb, w, err)) ok = false;
-        }
-        g.sync();
-        unsigned rem = g.ballot(v);
-        while (rem) {
-            const int f = __ffs(rem) - 1;
-            const uint64_t fd = g.shfl(d, f);
-            const bool dep = ((rem >> g.lane) & 1u) && g.lane > f && (sr + len > fd);
-            const unsigned dmask = g.ballot(dep);
-            const unsigned lim = dmask & (0u - dmask);
-            const unsigned batch = lim ? (rem & (lim - 1u)) : rem;
-            const bool mine = (batch >> g.lane) & 1u;
-            group_copy<G, kUnroll>(g, out, d, out + sr, mine ? len : 0u);
-            g.sync();
-            rem &= ~batch;
-        }
-    }
-    return ok;
-}
+// ------------------------------------------------ persistent schedule
 
-// Persistent decode: one cooperative launch; group k takes items k,
-// k + K, k + 2K, ... of the wave-major item list.  An item waits only for
-// items earlier in that list (its own block's earlier waves, and earlier
-// waves of the blocks its sources lie in), all groups are co-resident, and
-// each group takes its items in increasing order, so every wait ends.
-template <int G>
-__global__ void __launch_bounds__(kThreads) k_persistent(const uint4 *__restrict__ items,
-                                                         const uint32_t *__restrict__ next,
-                                                         uint64_t n_items, uint32_t *prog,
-                                                         const uint4 *__restrict__ tok,
-                                                         const uint8_t *__restrict__ lit,
-                                                         const uint64_t *__restrict__ blk_tok,
-                                                         const uint64_t *__restrict__ blk_lit,
-                                                         const uint32_t *__restrict__ slot, uint4 *tri,
-                                                         uint8_t *out, uint32_t log2bs, uint32_t *err) {
+// Waves >= 1 in one cooperative launch, by ranges: range r holds the
+// consecutive segments [s0, s1) of one wave (blocks in order).  Each match
+// waits (bounded) until every block its source touches has finished its
+// waves below w (per-block done bits; empty waves are preset), the range
+// copies all its matches together (only matches reading an earlier match
+// of the same block in the same pass are serialised), then sets bit w of
+// each of its blocks.  Ranges wait only for ranges of lower waves, earlier
+// in the list; all groups are co-resident and take their ranges in
+// increasing order (r, r + K, r + 2K, ...), so every wait ends.  STAGED: matches of at least kTmaMin bytes go through the group's
+// shared-memory stage by TMA bulk copies; otherwise all copies go through
+// registers and the kernel runs at higher occupancy.
+template <int G, bool STAGED>
+__global__ void __launch_bounds__(kThreads, STAGED ? 1 : 3)
+    k_ranges(const uint4 *__restrict__ ranges, uint64_t n_ranges, const uint4 *__restrict__ seg,
+             unsigned long long *done, uint32_t ww, const uint4 *__restrict__ tri, uint8_t *out,
+             uint32_t log2bs, uint32_t stage_bytes, uint32_t *err) {
+    extern __shared__ __align__(128) uint8_t smem[];
     Group<G> g;
+    constexpr int kGroups = kThreads / G;
+    Stage st;
+    uint32_t piece = 0;
+    if (STAGED) {
+        const int gi = threadIdx.x / G;
+        st.bar = reinterpret_cast<uint64_t *>(smem) + gi;
+        st.buf = smem + 128 * ((8 * kGroups + 127) / 128) + (size_t)gi * stage_bytes;
+        st.bytes = stage_bytes;
+        st.phase = 0;
+        if (g.lane == 0) mbar_init(st.bar, 1);
+        fence_mbar_init();
+        __syncthreads();
+        piece = min(kPiece, stage_bytes - 32u);
+    }
     const uint64_t gid = (blockIdx.x * (uint64_t)kThreads + threadIdx.x) / G;
-    const uint64_t ng = (uint64_t)gridDim.x * (kThreads / G);
+    const uint64_t ng = (uint64_t)gridDim.x * kGroups;
     bool ok = true;
-    for (uint64_t it = gid; it < n_items; it += ng) {
-        const uint4 item = __ldg(items + it);
-        const uint32_t b = item.x, w = item.y;
-        if (w == 0) {
-            block_wave0<G>(g, b, tok, lit, blk_tok, blk_lit, slot, tri, out, log2bs);
-        } else {
-            if (g.lane == 0 && !wait_at_least(prog + b, w, err)) ok = false;
+    // ranges[n_ranges] is a sentinel: the end of range r is ranges[r + 1].w
+    uint4 rn = gid < n_ranges ? __ldg(ranges + gid) : make_uint4(0, 0, 0, 0);
+    uint32_t tn = gid < n_ranges ? __ldg(ranges + gid + 1).w : 0u;
+    for (uint64_t it = gid; it < n_ranges; it += ng) {
+        const uint4 r = rn;
+        const uint64_t t_begin = r.w, t_end = tn;
+        if (it + ng < n_ranges) {  // next range's descriptor, loaded early
+            rn = __ldg(ranges + it + ng);
+            tn = __ldg(ranges + it + ng + 1).w;
+        }
+        const uint32_t w = r.x, s0 = r.y, s1 = r.z;
+        uint4 nt = t_begin + g.lane < t_end ? __ldg(tri + t_begin + g.lane) : make_uint4(0, 0, 0, 0);
+        for (uint64_t cur = t_begin; cur < t_end; cur += G) {
+            const uint64_t i = cur + g.lane;
+            const bool v = i < t_end;
+            const uint4 t = v ? nt : make_uint4(0, 0, 0, 0);
+            if (cur + G + g.lane < t_end) nt = __ldg(tri + cur + G + g.lane);
+            const uint64_t d = tri_dst(t), sr = tri_src(t);
+            const uint32_t len = v ? tri_len(t) : 0u;
+            const uint64_t blk = d >> log2bs;
+            // every block the source touches (its own included) has finished
+            // its waves below w
+            if (v) {
+                const uint64_t b0 = sr >> log2bs, b1 = (sr + len - 1) >> log2bs;
+                for (uint64_t bb = b0; bb <= b1; bb++)
+                    if (!wait_waves_below(done + bb * ww, w, err)) ok = false;
+            }
             g.sync();
-            if (!block_segment<G>(g, b, w, tri + item.z, item.w, prog, out, log2bs, err)) ok = false;
+            // segment starts inside this window (block changes)
+            uint64_t pblk = g.shfl_up(blk, 1);
+            if (g.lane == 0) pblk = ~0ULL;
+            const unsigned S = g.ballot(v && blk != pblk);
+            unsigned rem = g.ballot(v);
+            while (rem) {
+                if (STAGED) fence_proxy_async_global();
+                const int f = __ffs(rem) - 1;
+                const unsigned upto = (g.lane == G - 1) ? 0xffffffffu : ((2u << g.lane) - 1u);
+                const unsigned sm = (S | (1u << f)) & ~((1u << f) - 1u) & upto;
+                const int fs = sm ? 31 - __clz(sm) : f;
+                const uint64_t fsd = g.shfl(d, fs);
+                const bool dep = ((rem >> g.lane) & 1u) && g.lane > fs && (sr + len > fsd);
+                const unsigned dmask = g.ballot(dep);
+                const unsigned lim = dmask & (0u - dmask);
+                const unsigned batch = lim ? (rem & (lim - 1u)) : rem;
+                const bool mine = (batch >> g.lane) & 1u;
+                if (STAGED) {
+                    if (!hybrid_copy<G>(g, st, out, d, out + sr, mine ? len : 0u, kTmaMin, piece, err)) ok = false;
+                } else {
+                    group_copy<G, kUnrollCopy>(g, out, d, out + sr, mine ? len : 0u);
+                }
+                g.sync();
+                rem &= ~batch;
+            }
         }
         __threadfence();
         g.sync();
-        if (g.lane == 0) st_release(prog + b, __ldg(next + it));
+        const unsigned long long bit = 1ULL << (w % 64);
+        for (uint32_t k = s0 + g.lane; k < s1; k += G)
+            atomicOr(done + (uint64_t)__ldg(seg + k).x * ww + w / 64, bit);
     }
-    if (g.ballot(!ok) && g.lane == 0) atomicOr(err, kErrTimeout);
+    if (!ok) atomicOr(err, kErrTimeout);
 }
+
+// ------------------------------------------------------ wave schedule
 
 // Copy one wave's worklist.  Group k owns the segments (runs of one block)
 // that start in [k*T, (k+1)*T); a segment crossing the range end is
@@ -242,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_wave_copy(const uint4 *__restrict_
         unsigned rem = act;
         while (rem) {
             const int f = __ffs(rem) - 1;
-            const unsigned upto = (g.lane == 31) ? 0xffffffffu : ((2u << g.lane) - 1u);
+            const unsigned upto = (g.lane == G - 1) ? 0xffffffffu : ((2u << g.lane) - 1u);
             const unsigned sm = (S | (1u << f)) & ~((1u << f) - 1u) & upto;
             const int fs = sm ? 31 - __clz(sm) : f;
             const uint64_t fsd = g.shfl(d, fs);
@@ -251,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_wave_copy(const uint4 *__restrict_
             const unsigned lim = dmask & (0u - dmask);
             const unsigned batch = lim ? (rem & (lim - 1u)) : rem;
             const bool mine = (batch >> g.lane) & 1u;
-            group_copy<G, kUnroll>(g, out, d, out + sr, mine ? len : 0u);
+            group_copy<G, kUnrollCopy>(g, out, d, out + sr, mine ? len : 0u);
             g.sync();
             rem &= ~batch;
         }
@@ -265,7 +320,7 @@ int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st) {
     const unsigned grid0 = (h->n_blocks + gpc - 1) / gpc;
     k_wave0<G><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
                                             h->d_blk_lit, h->d_slot, (uint4 *)h->d_tri, out,
-                                            h->n_blocks, h->log2_bs);
+                                            h->n_blocks, h->log2_bs, nullptr, nullptr, 0);
     constexpr int ITEMS = 2;
     for (uint32_t w = 1; w < h->n_waves; w++) {
         const uint64_t a = h->wave_start[w], n = h->wave_start[w + 1] - a;
@@ -277,38 +332,109 @@ int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st) {
     return cudaGetLastError() == cudaSuccess ? ACLZ_OK : ACLZ_E_CUDA;
 }
 
-template <int G>
+struct Occ {
+    int per_sm = 0;
+    uint32_t stage_bytes = 0;
+    size_t smem = 0;
+};
+
+// Dynamic shared memory limit last set on each staged kernel instance.
+template <int G, bool STAGED>
+size_t &smem_attr() {
+    static size_t v = 0;
+    return v;
+}
+
+// Persistent mode: the wave-0 kernel (no dependencies) initialises the
+// per-block done bits, then one cooperative launch runs every range of
+// waves >= 1.
+template <int G, bool STAGED>
 int launch_persistent(aclz_handle *h, uint8_t *out, uint32_t ctas_per_sm, cudaStream_t st) {
-    static int max_per_sm = -1, sms = 0;
-    auto fn = k_persistent<G>;
-    if (max_per_sm < 0) {
+    constexpr int gpc = kThreads / G;
+    const unsigned grid0 = (h->n_blocks + gpc - 1) / gpc;
+    k_wave0<G><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
+                                            h->d_blk_lit, h->d_slot, (uint4 *)h->d_tri, out,
+                                            h->n_blocks, h->log2_bs, h->d_pending, h->d_done,
+                                            h->n_wave_words);
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
+        note_cuda_error(e);
+        return ACLZ_E_CUDA;
+    }
+    if (!h->n_ranges) return ACLZ_OK;
+    auto fn = k_ranges<G, STAGED>;
+    static int sms = 0;
+    static Occ occ[5][33];  // [ctas_per_sm request 0..4][G]
+    const uint32_t req = std::min<uint32_t>(ctas_per_sm, 4);
+    Occ &o = occ[req][G];
+    if (!o.per_sm) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (STAGED) {
+            cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            const uint32_t cps = req ? req : 1;
+            const size_t bar = 128 * ((8 * gpc + 127) / 128);
+            o.stage_bytes = (uint32_t)(((kSmemPerSm / cps - bar) / gpc) & ~127u);
+            o.smem = bar + (size_t)gpc * o.stage_bytes;
+            if (cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem);
+                e != cudaSuccess) {
+                note_cuda_error(e);
+                return ACLZ_E_CUDA;
+            }
+            smem_attr<G, STAGED>() = o.smem;
+        }
         int m = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, fn, kThreads, 0) != cudaSuccess) return ACLZ_E_CUDA;
-        max_per_sm = m;
+        if (cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, fn, kThreads, o.smem);
+            e != cudaSuccess) {
+            note_cuda_error(e);
+            return ACLZ_E_CUDA;
+        }
+        if (!STAGED && req && (int)req < m) m = (int)req;
+        o.per_sm = m > 0 ? m : -1;
     }
-    int per_sm = max_per_sm;
-    if (ctas_per_sm && (int)ctas_per_sm < per_sm) per_sm = (int)ctas_per_sm;
-    if (per_sm < 1) return ACLZ_E_UNSUPPORTED;
-    uint64_t need = (h->n_items + (kThreads / G) - 1) / (kThreads / G);
-    unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)per_sm * sms, need ? need : 1);
-    if (cudaMemsetAsync(h->d_prog, 0, 4 * (size_t)h->n_blocks, st) != cudaSuccess) return ACLZ_E_CUDA;
-    const uint4 *items = (const uint4 *)h->d_items;
-    const uint32_t *next = h->d_next;
-    uint64_t n_items = h->n_items;
-    uint32_t *prog = h->d_prog;
-    const uint4 *tok = (const uint4 *)h->d_tok;
-    const uint8_t *lit = h->d_lit;
-    const uint64_t *bt = h->d_blk_tok, *bl = h->d_blk_lit;
-    const uint32_t *slot = h->d_slot;
-    uint4 *tri = (uint4 *)h->d_tri;
+    if (o.per_sm < 1) return ACLZ_E_UNSUPPORTED;
+    if (STAGED && smem_attr<G, STAGED>() != o.smem) {
+        if (cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem);
+            e != cudaSuccess) {
+            note_cuda_error(e);
+            return ACLZ_E_CUDA;
+        }
+        smem_attr<G, STAGED>() = o.smem;
+    }
+    const uint64_t need = (h->n_ranges + gpc - 1) / gpc;
+    unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)o.per_sm * sms, need ? need : 1);
+    const uint4 *ranges = (const uint4 *)h->d_ranges;
+    uint64_t n_ranges = h->n_ranges;
+    const uint4 *seg = (const uint4 *)h->d_seg;
+    unsigned long long *done = (unsigned long long *)h->d_done;
+    uint32_t ww = h->n_wave_words;
+    const uint4 *tri = (const uint4 *)h->d_tri;
     uint32_t log2bs = h->log2_bs;
+    uint32_t sb = o.stage_bytes;
     uint32_t *err = h->d_err;
-    void *args[] = {&items, &next, &n_items, &prog, &tok, &lit, &bt, &bl, &slot, &tri, &out, &log2bs, &err};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kThreads), args, 0, st);
-    return e == cudaSuccess ? ACLZ_OK : ACLZ_E_CUDA;
+    void *args[] = {&ranges, &n_ranges, &seg, &done, &ww, &tri, &out, &log2bs, &sb, &err};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kThreads), args, o.smem, st);
+    if (e == cudaErrorCooperativeLaunchTooLarge && o.per_sm > 1) {
+        // fewer co-resident CTAs than the occupancy estimate: one per SM
+        cudaGetLastError();
+        o.per_sm = 1;
+        grid = (unsigned)std::min<uint64_t>((uint64_t)sms, need ? need : 1);
+        e = cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kThreads), args, o.smem, st);
+    }
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        return ACLZ_E_CUDA;
+    }
+    return ACLZ_OK;
+}
+
+template <int G>
+int launch_persistent_auto(aclz_handle *h, uint8_t *out, const aclz_decode_cfg &c, cudaStream_t st) {
+    bool staged = h->mean_deferred_len >= (double)kTmaMin;
+    if (c.flags & ACLZ_FLAG_STAGED) staged = true;
+    if (c.flags & ACLZ_FLAG_REGISTERS) staged = false;
+    return staged ? launch_persistent<G, true>(h, out, c.ctas_per_sm, st)
+                  : launch_persistent<G, false>(h, out, c.ctas_per_sm, st);
 }
 
 }  // namespace
@@ -318,18 +444,19 @@ extern "C" int aclz_decode_all(aclz_handle *h, void *d_out, uint64_t cap, const 
     if (!h || (!d_out && h->total_len)) return ACLZ_E_INVAL;
     if (cap < h->total_len) return ACLZ_E_CAPACITY;
     if (reinterpret_cast<uintptr_t>(d_out) & 15) return ACLZ_E_INVAL;
-    aclz_decode_cfg c = {32, ACLZ_MODE_WAVES, 0, 0};
+    aclz_decode_cfg c = {32, ACLZ_MODE_PERSISTENT, 0, 0};
     if (cfg) c = *cfg;
     if (c.G != 8 && c.G != 16 && c.G != 32) return ACLZ_E_INVAL;
     if (c.mode != ACLZ_MODE_WAVES && c.mode != ACLZ_MODE_PERSISTENT) return ACLZ_E_INVAL;
+    if ((c.flags & ACLZ_FLAG_STAGED) && (c.flags & ACLZ_FLAG_REGISTERS)) return ACLZ_E_INVAL;
     if (h->n_blocks == 0) return ACLZ_OK;
     cudaStream_t st = (cudaStream_t)stream;
     uint8_t *out = (uint8_t *)d_out;
     if (c.mode == ACLZ_MODE_PERSISTENT) {
         switch (c.G) {
-            case 8: return launch_persistent<8>(h, out, c.ctas_per_sm, st);
-            case 16: return launch_persistent<16>(h, out, c.ctas_per_sm, st);
-            default: return launch_persistent<32>(h, out, c.ctas_per_sm, st);
+            case 8: return launch_persistent_auto<8>(h, out, c, st);
+            case 16: return launch_persistent_auto<16>(h, out, c, st);
+            default: return launch_persistent_auto<32>(h, out, c, st);
         }
     }
     switch (c.G) {

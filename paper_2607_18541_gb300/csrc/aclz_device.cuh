@@ -53,6 +53,22 @@ __device__ __forceinline__ uint4 ldcg16(const uint8_t *p) {
     return __ldcg(reinterpret_cast<const uint4 *>(p));
 }
 
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint4 lds16(const uint8_t *p) {
+    uint4 v;
+    asm("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(smem_u32(p)));
+    return v;
+}
+
+__device__ __forceinline__ uint4 lds16_u32(uint32_t a) {
+    uint4 v;
+    asm("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
 // Bytes [r, r + 16) of the 32-byte little-endian concatenation a || b.
 __device__ __forceinline__ uint4 window16(uint4 a, uint4 b, uint32_t r) {
     uint32_t v0 = a.x, v1 = a.y, v2 = a.z, v3 = a.w, v4 = b.x, v5 = b.y, v6 = b.z, v7 = b.w;
@@ -70,44 +86,56 @@ __device__ __forceinline__ uint4 window16(uint4 a, uint4 b, uint32_t r) {
     return o;
 }
 
-// Store bytes [lo, hi) of the 16-byte word v at the aligned address p.
+// Store bytes [lo, hi) of the 16-byte word v at the aligned address p,
+// as at most seven naturally aligned 1/2/4/8-byte stores.
 __device__ __forceinline__ void store_partial16(uint8_t *p, uint4 v, uint32_t lo, uint32_t hi) {
-    uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (uint32_t t = 0; t < 16; t++) {
-        if (t >= lo && t < hi) p[t] = (uint8_t)(w[t >> 2] >> (8 * (t & 3)));
-    }
+    const unsigned long long q0 = (unsigned long long)v.x | ((unsigned long long)v.y << 32);
+    const unsigned long long q1 = (unsigned long long)v.z | ((unsigned long long)v.w << 32);
+    // byte t of the word, t in [0, 16), and the little-endian field at t
+    auto field = [&](uint32_t t) -> unsigned long long { return t < 8 ? (q0 >> (8 * t)) | (t ? q1 << (64 - 8 * t) : 0ULL) : q1 >> (8 * (t - 8)); };
+    uint32_t t = lo;
+    if ((t & 1) && t + 1 <= hi) { p[t] = (uint8_t)field(t); t += 1; }
+    if ((t & 2) && t + 2 <= hi) { *reinterpret_cast<uint16_t *>(p + t) = (uint16_t)field(t); t += 2; }
+    if ((t & 4) && t + 4 <= hi) { *reinterpret_cast<uint32_t *>(p + t) = (uint32_t)field(t); t += 4; }
+    if ((t & 8) && t + 8 <= hi) { *reinterpret_cast<unsigned long long *>(p + t) = field(t); t += 8; }
+    while (t + 8 <= hi) { *reinterpret_cast<unsigned long long *>(p + t) = field(t); t += 8; }
+    if (t + 4 <= hi) { *reinterpret_cast<uint32_t *>(p + t) = (uint32_t)field(t); t += 4; }
+    if (t + 2 <= hi) { *reinterpret_cast<uint16_t *>(p + t) = (uint16_t)field(t); t += 2; }
+    if (t + 1 <= hi) { p[t] = (uint8_t)field(t); }
 }
 
 // One aligned 16-byte output chunk of a copy job: output bytes
-// [A + lo, A + hi) receive source bytes starting at s (s is the source of
-// output byte A + lo).  Loads only the aligned source words that hold
-// needed bytes, so reads never leave the 16-byte words of the source range.
-struct Chunk {
-    uint8_t *dst;       // A, 16-byte aligned
-    const uint8_t *s;   // source of byte A + lo
-    uint32_t lo, hi;    // 0 <= lo < hi <= 16
-};
-
-__device__ __forceinline__ void chunk_load(const Chunk &c, uint4 &w0, uint4 &w1, uint32_t &r) {
-    // virtual source of output byte A is s - lo
-    const uintptr_t vs = reinterpret_cast<uintptr_t>(c.s) - c.lo;
+// [A + lo, A + hi) receive source bytes starting at s (the source of
+// output byte A + lo).  Only the aligned source words holding needed bytes
+// are read, so reads never leave the 16-byte words of the source range.
+// SMEM: the source is a shared-memory staging copy whose addresses are
+// congruent mod 16 to the global source.
+template <bool SMEM>
+__device__ __forceinline__ void chunk_load(const uint8_t *s, uint32_t lo, uint32_t hi, uint4 &w0, uint4 &w1,
+                                           uint32_t &r) {
+    const uintptr_t vs = reinterpret_cast<uintptr_t>(s) - lo;
     const uintptr_t base = vs & ~(uintptr_t)15;
     r = (uint32_t)(vs & 15);
-    const uintptr_t s0 = reinterpret_cast<uintptr_t>(c.s);
-    const uintptr_t s1 = s0 + (c.hi - c.lo);  // one past the last needed source byte
+    const uintptr_t s0 = reinterpret_cast<uintptr_t>(s);
+    const uintptr_t s1 = s0 + (hi - lo);  // one past the last needed source byte
     w0 = make_uint4(0, 0, 0, 0);
     w1 = make_uint4(0, 0, 0, 0);
-    if (base + 16 > s0) w0 = ldcg16(reinterpret_cast<const uint8_t *>(base));
-    if (s1 > base + 16) w1 = ldcg16(reinterpret_cast<const uint8_t *>(base + 16));
+    if (SMEM) {
+        if (base + 16 > s0) w0 = lds16(reinterpret_cast<const uint8_t *>(base));
+        if (s1 > base + 16) w1 = lds16(reinterpret_cast<const uint8_t *>(base + 16));
+    } else {
+        if (base + 16 > s0) w0 = ldcg16(reinterpret_cast<const uint8_t *>(base));
+        if (s1 > base + 16) w1 = ldcg16(reinterpret_cast<const uint8_t *>(base + 16));
+    }
 }
 
-__device__ __forceinline__ void chunk_store(const Chunk &c, uint4 w0, uint4 w1, uint32_t r) {
+__device__ __forceinline__ void chunk_store(uint8_t *dst, uint32_t lo, uint32_t hi, uint4 w0, uint4 w1,
+                                            uint32_t r) {
     uint4 v = window16(w0, w1, r);
-    if (c.lo == 0 && c.hi == 16)
-        *reinterpret_cast<uint4 *>(c.dst) = v;
+    if (lo == 0 && hi == 16)
+        *reinterpret_cast<uint4 *>(dst) = v;
     else
-        store_partial16(c.dst, v, c.lo, c.hi);
+        store_partial16(dst, v, lo, hi);
 }
 
 // Packed group copy.  Each lane holds one job (d: output offset, s: source
@@ -115,21 +143,20 @@ __device__ __forceinline__ void chunk_store(const Chunk &c, uint4 w0, uint4 w1, 
 // numbered in lane order and dealt to the group's lanes, U per lane per
 // round, loads issued before stores.  Jobs must be independent: no job's
 // source may overlap another job's output in the same call.
-template <int G, int U>
+template <int G, int U, bool SMEM = false>
 __device__ __forceinline__ void group_copy(const Group<G> &g, uint8_t *out, uint64_t d,
                                            const uint8_t *s, uint32_t n) {
     const uint32_t c = n ? (uint32_t)(((d + n - 1) >> 4) - (d >> 4) + 1) : 0u;
     const uint32_t incl = g.scan_incl(c);
     const uint32_t total = g.shfl(incl, G - 1);
     for (uint32_t base = 0; base < total; base += (uint32_t)G * U) {
-        Chunk ch[U];
+        uint8_t *dst[U];
+        uint32_t lohi[U];
         uint4 a[U], b[U];
         uint32_t r[U];
-        bool act[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const uint32_t k = base + (uint32_t)u * G + (uint32_t)g.lane;
-            act[u] = k < total;
             // owner: first lane j with incl_j > k
             int lo = 0, hi = G - 1;
 #pragma unroll
@@ -139,26 +166,200 @@ __device__ __forceinline__ void group_copy(const Group<G> &g, uint8_t *out, uint
                 if (v > k) hi = mid; else lo = mid + 1;
             }
             const int j = lo;
-            const uint32_t cj = g.shfl(c, j);
-            const uint32_t ej = g.shfl(incl, j) - cj;
+            const uint32_t ej = g.shfl(incl, j) - g.shfl(c, j);
             const uint64_t dj = g.shfl(d, j);
             const uint8_t *sj = reinterpret_cast<const uint8_t *>(
                 g.shfl(reinterpret_cast<unsigned long long>(s), j));
             const uint32_t nj = g.shfl(n, j);
-            const uint32_t q = k - ej;
-            const uint64_t A = ((dj >> 4) + q) << 4;
+            const uint64_t A = ((dj >> 4) + (k - ej)) << 4;
             const uint64_t blo = dj > A ? dj : A;
             const uint64_t bhi = (dj + nj) < (A + 16) ? (dj + nj) : (A + 16);
-            ch[u].dst = out + A;
-            ch[u].s = sj + (blo - dj);
-            ch[u].lo = (uint32_t)(blo - A);
-            ch[u].hi = (uint32_t)(bhi - A);
-            if (act[u]) chunk_load(ch[u], a[u], b[u], r[u]);
+            const uint32_t clo = (uint32_t)(blo - A), chi = (uint32_t)(bhi - A);
+            dst[u] = out + A;
+            lohi[u] = k < total ? (clo | (chi << 8)) : 0u;
+            if (k < total) chunk_load<SMEM>(sj + (blo - dj), clo, chi, a[u], b[u], r[u]);
         }
 #pragma unroll
         for (int u = 0; u < U; u++)
-            if (act[u]) chunk_store(ch[u], a[u], b[u], r[u]);
+            if (lohi[u]) chunk_store(dst[u], lohi[u] & 0xff, lohi[u] >> 8, a[u], b[u], r[u]);
     }
+}
+
+// ------------------------------------------------------- TMA staging
+
+// Per-group staging area for 1-D bulk copies (cp.async.bulk) from global
+// memory into shared memory, tracked by one mbarrier (transaction bytes).
+struct Stage {
+    uint8_t *buf;
+    uint64_t *bar;
+    uint32_t bytes;
+    uint32_t phase;
+};
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// orders this thread's view of global memory (including data acquired from
+// other threads) before its later bulk-copy reads
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void *dst_smem, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr uint32_t kMbarSpinLimit = 1u << 26;
+
+// Wait for the stage's current phase (bounded; sets kErrTimeout on err).
+__device__ __forceinline__ bool stage_wait(Stage &st, uint32_t *err) {
+    uint32_t spins = 0;
+    bool ok = true;
+    while (!mbar_try_wait(st.bar, st.phase)) {
+        if (++spins > kMbarSpinLimit) {
+            atomicOr(err, kErrTimeout);
+            ok = false;
+            break;
+        }
+    }
+    st.phase ^= 1u;
+    return ok;
+}
+
+// Bytes [r, r + 16) of a || b for a shift r that is the same on every lane
+// (a uniform branch picks the word offset).
+__device__ __forceinline__ uint4 window16_uniform(const uint4 &a, const uint4 &b, uint32_t q, uint32_t sh) {
+    uint32_t w0, w1, w2, w3, w4;
+    switch (q) {
+        case 0: w0 = a.x; w1 = a.y; w2 = a.z; w3 = a.w; w4 = b.x; break;
+        case 1: w0 = a.y; w1 = a.z; w2 = a.w; w3 = b.x; w4 = b.y; break;
+        case 2: w0 = a.z; w1 = a.w; w2 = b.x; w3 = b.y; w4 = b.z; break;
+        default: w0 = a.w; w1 = b.x; w2 = b.y; w3 = b.z; w4 = b.w; break;
+    }
+    uint4 o;
+    o.x = __funnelshift_r(w0, w1, sh);
+    o.y = __funnelshift_r(w1, w2, sh);
+    o.z = __funnelshift_r(w2, w3, sh);
+    o.w = __funnelshift_r(w3, w4, sh);
+    return o;
+}
+
+// Realign-and-store of one staged job: output [d, d + n) from the shared
+// copy at s (congruent to the global source mod 16).  The partial head and
+// tail words go out as single bytes, one per lane, in one pass (a chain of
+// narrow stores from one lane is far slower); the aligned 16-byte body
+// words go to consecutive lanes, two per lane per round, each built from
+// two aligned shared words and one shift common to the whole job.
+template <int G>
+__device__ __forceinline__ void store_staged_job(const Group<G> &g, uint8_t *out, uint64_t d,
+                                                 const uint8_t *s, uint32_t n) {
+    const uint64_t e = d + n;
+    uint64_t a0 = (d + 15) & ~(uint64_t)15;  // first aligned body word
+    uint64_t a1 = e & ~(uint64_t)15;         // end of the aligned body
+    if (a0 > e) a0 = e;
+    if (a1 < a0) a1 = a0;
+    const uint32_t nh = (uint32_t)(a0 - d), nt = (uint32_t)(e - a1);
+    for (uint32_t t = g.lane; t < nh + nt; t += G) {
+        const uint32_t o = t < nh ? t : (uint32_t)(a1 - d) + (t - nh);
+        out[d + o] = s[o];
+    }
+    if (a1 <= a0) return;
+    // body: source of output word a0 + 16k is shared byte sa + (a0 - d) + 16k
+    const uint32_t sb = smem_u32(s) + (uint32_t)(a0 - d);
+    const uint32_t r = sb & 15u, base = sb & ~15u, q = r >> 2, sh = (r & 3u) * 8u;
+    const uint32_t nw = (uint32_t)((a1 - a0) >> 4);
+    uint8_t *ob = out + a0;
+    for (uint32_t k = g.lane; k < nw; k += 2 * G) {
+        const uint32_t k2 = k + G;
+        uint4 x0 = lds16_u32(base + 16 * k), y0 = make_uint4(0, 0, 0, 0);
+        uint4 x1 = make_uint4(0, 0, 0, 0), y1 = make_uint4(0, 0, 0, 0);
+        if (r) y0 = lds16_u32(base + 16 * k + 16);
+        if (k2 < nw) {
+            x1 = lds16_u32(base + 16 * k2);
+            if (r) y1 = lds16_u32(base + 16 * k2 + 16);
+        }
+        *reinterpret_cast<uint4 *>(ob + 16 * (uint64_t)k) = r ? window16_uniform(x0, y0, q, sh) : x0;
+        if (k2 < nw) *reinterpret_cast<uint4 *>(ob + 16 * (uint64_t)k2) = r ? window16_uniform(x1, y1, q, sh) : x1;
+    }
+}
+
+// Copy jobs through shared memory: every lane's job (d, s, n) is cut into
+// pieces of at most `piece` bytes; the aligned source span of each piece
+// is fetched by one bulk copy into the stage (packed in lane order, as
+// many as fit), then the group realigns the bytes from shared memory and
+// writes aligned 16-byte words to the output, one job at a time.  The
+// caller has made the source bytes final and visible to bulk copies
+// (fence_proxy_async_global after acquiring them).  Jobs must be
+// independent.
+template <int G>
+__device__ __forceinline__ bool staged_copy(const Group<G> &g, Stage &st, uint8_t *out, uint64_t d,
+                                            const uint8_t *s, uint32_t n, uint32_t piece, uint32_t *err) {
+    bool ok = true;
+    uint32_t done = 0;
+    for (;;) {
+        const uint32_t rem = n - done;
+        if (!g.ballot(rem > 0)) break;
+        const uint32_t len = rem < piece ? rem : piece;
+        const uintptr_t ps = reinterpret_cast<uintptr_t>(s) + done;
+        const uintptr_t sa = ps & ~(uintptr_t)15;
+        const uint32_t span = rem ? (uint32_t)(((ps + len + 15) & ~(uintptr_t)15) - sa) : 0u;
+        const uint32_t incl = g.scan_incl(span);
+        const bool take = rem > 0 && incl <= st.bytes;
+        const unsigned tm = g.ballot(take);
+        const int last = 31 - __clz(tm);
+        const uint32_t tx = g.shfl(incl, last);
+        if (g.lane == 0) mbar_expect_tx(st.bar, tx);
+        g.sync();
+        const uint32_t off = incl - span;
+        if (take) tma_load_1d(st.buf + off, reinterpret_cast<const void *>(sa), span, st.bar);
+        if (!stage_wait(st, err)) ok = false;
+        const uint8_t *src = st.buf + off + (uint32_t)(ps - sa);
+        for (unsigned m = tm; m; m &= m - 1) {
+            const int j = __ffs(m) - 1;
+            const uint64_t dj = g.shfl(d + done, j);
+            const uint8_t *sj =
+                reinterpret_cast<const uint8_t *>(g.shfl(reinterpret_cast<unsigned long long>(src), j));
+            const uint32_t nj = g.shfl(len, j);
+            store_staged_job<G>(g, out, dj, sj, nj);
+        }
+        g.sync();
+        fence_proxy_async_shared();
+        if (take) done += len;
+    }
+    return ok;
+}
+
+// Short jobs through registers, long ones through the stage.
+template <int G>
+__device__ __forceinline__ bool hybrid_copy(const Group<G> &g, Stage &st, uint8_t *out, uint64_t d,
+                                            const uint8_t *s, uint32_t n, uint32_t tma_min, uint32_t piece,
+                                            uint32_t *err) {
+    const bool longj = n >= tma_min;
+    group_copy<G, 2>(g, out, d, s, longj ? 0u : n);
+    if (!g.ballot(longj)) return true;
+    return staged_copy<G>(g, st, out, d, s, longj ? n : 0u, piece, err);
 }
 
 }  // namespace aclz

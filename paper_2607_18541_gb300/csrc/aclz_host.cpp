@@ -169,6 +169,12 @@ void parse_block(const uint8_t *x, uint64_t n, uint64_t bstart, uint64_t bend, c
 
 namespace aclz {
 
+namespace {
+std::atomic<int> g_last_cuda_error{0};
+}
+
+void note_cuda_error(int cuda_error_code) { g_last_cuda_error.store(cuda_error_code); }
+
 int parse_container(const uint8_t *c, uint64_t n, View *v, bool check_directory) {
     if (!c || n < kHdr) return ACLZ_E_CORRUPT;
     if (c[0] != 'A' || c[1] != 'C' || c[2] != 'L' || c[3] != 'Z') return ACLZ_E_CORRUPT;
@@ -371,6 +377,8 @@ int aclz_container_info(const void *host_buf, uint64_t n, aclz_info *out) {
     std::memcpy(out->min_match, v.mm, 4);
     return ACLZ_OK;
 }
+
+int aclz_last_cuda_error(void) { return g_last_cuda_error.load(); }
 
 const char *aclz_strerror(int code) {
     switch (code) {

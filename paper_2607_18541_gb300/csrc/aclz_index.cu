@@ -245,18 +245,25 @@ __global__ void k_store_tags(uint4 *tok, const uint32_t *tags, uint64_t n) {
     }
 }
 
-// counts per (wave >= 1, block), wave-major
+// counts per (wave >= 1, block), wave-major, and the deferred bytes
 __global__ void __launch_bounds__(256) k_wave_hist(const uint4 *__restrict__ tok,
                                                    const uint64_t *__restrict__ blk_tok,
-                                                   uint32_t *cnt, uint32_t nb) {
+                                                   uint32_t *cnt, uint32_t nb,
+                                                   unsigned long long *def_bytes) {
     const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= nb) return;
+    unsigned long long bytes = 0;
     for (uint64_t i = blk_tok[b] + lane; i < blk_tok[b + 1]; i += 32) {
         const uint4 t = __ldg(tok + i);
         const uint32_t tg = t.w >> 8;
-        if (t.y && tg) atomicAdd(cnt + (uint64_t)(tg - 1) * nb + b, 1u);
+        if (t.y && tg) {
+            atomicAdd(cnt + (uint64_t)(tg - 1) * nb + b, 1u);
+            bytes += t.y;
+        }
     }
+    for (int o = 16; o; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+    if (lane == 0 && bytes) atomicAdd(def_bytes, bytes);
 }
 
 // slot of every deferred match: its (wave, block) segment base plus its
@@ -298,28 +305,70 @@ __global__ void k_seg_flags(const uint32_t *base, uint64_t M, const uint32_t *to
     }
 }
 
-// Work items of the persistent decode, wave-major: item b = wave 0 of
-// block b; then one item per non-empty (wave, block) segment, placed by the
-// compaction scan pos.  next[i] = the block's next non-empty wave after
-// item i (0xffffffff when none).
-__global__ void k_items_build(const uint32_t *base, const uint32_t *pos, const uint32_t *total,
-                              uint32_t nb, uint32_t nw1, uint4 *items, uint32_t *next) {
+// Segments of the persistent decode, wave-major: seg[pos[k]] for every
+// non-empty (wave, block) cell k, and the block's pending-wave bits.
+__global__ void k_segs_build(const uint32_t *base, const uint32_t *pos, const uint32_t *total,
+                             uint32_t nb, uint32_t nw1, uint32_t ww, uint4 *seg,
+                             unsigned long long *pending) {
     const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     const uint64_t M = (uint64_t)nw1 * nb;
-    items[b] = make_uint4(b, 0u, 0u, 0u);
-    uint64_t prev = b;
+    unsigned long long word = 1ULL;  // wave 0
+    uint32_t wk = 0;
     for (uint32_t w = 1; w <= nw1; w++) {
+        if (w / 64 != wk) {
+            pending[(uint64_t)b * ww + wk] = word;
+            wk = w / 64;
+            word = 0;
+        }
         const uint64_t k = (uint64_t)(w - 1) * nb + b;
         const uint32_t nxt = k + 1 < M ? base[k + 1] : *total;
         const uint32_t c = nxt - base[k];
         if (!c) continue;
-        const uint64_t idx = nb + pos[k];
-        items[idx] = make_uint4(b, w, base[k], c);
-        next[prev] = w;
-        prev = idx;
+        seg[pos[k]] = make_uint4(b, w, base[k], c);
+        word |= 1ULL << (w % 64);
     }
-    next[prev] = 0xffffffffu;
+    pending[(uint64_t)b * ww + wk] = word;
+    for (uint32_t k2 = wk + 1; k2 < ww; k2++) pending[(uint64_t)b * ww + k2] = 0;
+}
+
+// A range starts at segment s when s begins a wave or its first triplet
+// falls in a new multiple of T.
+__global__ void k_range_flags(const uint4 *seg, uint64_t n, uint32_t T, uint32_t *flag) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 a = seg[s];
+        bool f = s == 0;
+        if (!f) {
+            const uint4 p = seg[s - 1];
+            f = a.y != p.y || (a.z / T) != (p.z / T);
+        }
+        flag[s] = f ? 1u : 0u;
+    }
+}
+
+// ex is the exclusive scan of the range-start flags, nr their sum:
+// segment s starts range ex[s] when ex[s + 1] > ex[s].  ranges[r] =
+// {wave, first segment, end segment, first triplet}; ranges[nr] is a
+// sentinel whose first triplet is the end of the last range.
+__global__ void k_range_build(const uint4 *seg, const uint32_t *ex, uint64_t n, uint32_t nr,
+                              uint32_t n_tri, uint4 *ranges) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = ex[s];
+        const uint32_t nx = s + 1 < n ? ex[s + 1] : nr;
+        if (nx > r) {
+            const uint4 a = seg[s];
+            ranges[r].x = a.y;
+            ranges[r].y = (uint32_t)s;
+            ranges[r].w = a.z;
+            if (r > 0) ranges[r - 1].z = (uint32_t)s;
+        }
+        if (s + 1 == n) {
+            ranges[nr - 1].z = (uint32_t)n;
+            ranges[nr] = make_uint4(0u, (uint32_t)n, (uint32_t)n, n_tri);
+        }
+    }
 }
 
 // ------------------------------------------------- exclusive scan (u32)
@@ -491,8 +540,10 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
     DevBuf work;
     CK(cudaMalloc(&work.p, 64));
     uint32_t *d_maxtag = (uint32_t *)work.p, *d_ctr = d_maxtag + 1, *d_total = d_maxtag + 2;
-    unsigned long long *d_first_bad = (unsigned long long *)((char *)work.p + 16);
-    CK(cudaMemsetAsync(work.p, 0, 16, st));
+    // words: [0] max tag, [1] counter, [2] deferred total, [3] segment count,
+    // [4] range count; bytes 32..39: first bad token
+    unsigned long long *d_first_bad = (unsigned long long *)((char *)work.p + 32);
+    CK(cudaMemsetAsync(work.p, 0, 32, st));
     CK(cudaMemsetAsync(d_first_bad, 0xff, 8, st));
     const unsigned wblocks = (nb + 7) / 8;  // 8 warps per CTA
     const bool has_tags = (v.flags & kFlagWaves) != 0;
@@ -539,6 +590,7 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
     h->n_waves = maxtag + 1;
     h->wave_start.assign(h->n_waves + 1, 0);
     CK(cudaMemsetAsync(h->d_slot, 0xff, 4 * nt, st));
+    unsigned long long defb_total = 0;
     if (maxtag > 0) {
         const uint64_t M = (uint64_t)maxtag * nb;
         if (M > (1ULL << 31)) { cleanup(); return ACLZ_E_UNSUPPORTED; }
@@ -546,14 +598,17 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
         CK(cudaMalloc(&cnt.p, 4 * M));
         CK(cudaMalloc(&starts.p, 8 * (maxtag + 1)));
         CK(cudaMemsetAsync(cnt.p, 0, 4 * M, st));
-        k_wave_hist<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, (uint32_t *)cnt.p, nb);
+        unsigned long long *d_def_bytes = (unsigned long long *)((char *)work.p + 40);
+        CK(cudaMemsetAsync(d_def_bytes, 0, 8, st));
+        k_wave_hist<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, (uint32_t *)cnt.p, nb,
+                                              d_def_bytes);
         CK(cudaGetLastError());
         rc = device_excl_scan((uint32_t *)cnt.p, M, d_total, st);
         if (rc) { cleanup(); return rc; }
         k_gather_starts<<<(maxtag + 256) / 256, 256, 0, st>>>((const uint32_t *)cnt.p, nb, maxtag, d_total,
                                                             (uint64_t *)starts.p);
-        // persistent-mode items from the segment bases (before k_slots turns
-        // the bases into cursors)
+        // persistent-mode segments and ranges, from the segment bases
+        // (before k_slots turns the bases into cursors)
         {
             DevBuf flag;
             CK(cudaMalloc(&flag.p, 4 * M));
@@ -564,13 +619,17 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
             uint32_t nseg = 0;
             CK(cudaMemcpyAsync(&nseg, d_nseg, 4, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            h->n_items = (uint64_t)nb + nseg;
-            CK(cudaMalloc(&h->d_items, 16 * h->n_items));
-            CK(cudaMalloc((void **)&h->d_next, 4 * h->n_items));
-            k_items_build<<<(nb + 255) / 256, 256, 0, st>>>((const uint32_t *)cnt.p, (const uint32_t *)flag.p,
-                                                           d_total, nb, maxtag, (uint4 *)h->d_items,
-                                                           h->d_next);
+            h->n_seg = nseg;
+            h->n_wave_words = (maxtag + 1 + 63) / 64;
+            CK(cudaMalloc(&h->d_seg, 16 * (size_t)(nseg ? nseg : 1)));
+            CK(cudaMalloc((void **)&h->d_pending, 8 * (size_t)nb * h->n_wave_words));
+            k_segs_build<<<(nb + 255) / 256, 256, 0, st>>>((const uint32_t *)cnt.p, (const uint32_t *)flag.p,
+                                                          d_total, nb, maxtag, h->n_wave_words,
+                                                          (uint4 *)h->d_seg,
+                                                          (unsigned long long *)h->d_pending);
             CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(&defb_total, d_def_bytes, 8, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
             CK(cudaStreamSynchronize(st));
         }
         k_slots<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, (uint32_t *)cnt.p,
@@ -581,17 +640,17 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
         CK(cudaStreamSynchronize(st));
         h->n_deferred = h->wave_start[h->n_waves];
         if (h->n_deferred) CK(cudaMalloc(&h->d_tri, 16 * h->n_deferred));
+        h->mean_deferred_len = h->n_deferred ? (double)defb_total / (double)h->n_deferred : 0.0;
+        rc = aclz_set_range_bytes(h, h->range_bytes, stream);
+        if (rc) { cleanup(); return rc; }
     }
-    if (!h->d_items) {
-        h->n_items = nb;
-        CK(cudaMalloc(&h->d_items, 16 * h->n_items));
-        CK(cudaMalloc((void **)&h->d_next, 4 * h->n_items));
-        std::vector<uint32_t> it(4 * (size_t)nb), nx(nb, 0xffffffffu);
-        for (uint32_t b = 0; b < nb; b++) { it[4 * b] = b; it[4 * b + 1] = it[4 * b + 2] = it[4 * b + 3] = 0; }
-        CK(cudaMemcpyAsync(h->d_items, it.data(), 16 * (size_t)nb, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(h->d_next, nx.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, st));
+    if (!h->d_pending) {  // no deferred matches: wave 0 finishes every block
+        h->n_wave_words = 1;
+        std::vector<uint64_t> ones(nb, 1ULL);
+        CK(cudaMalloc((void **)&h->d_pending, 8 * (size_t)nb));
+        CK(cudaMemcpyAsync(h->d_pending, ones.data(), 8 * (size_t)nb, cudaMemcpyHostToDevice, st));
     }
-    CK(cudaMalloc((void **)&h->d_prog, 4 * (size_t)nb));
+    CK(cudaMalloc((void **)&h->d_done, 8 * (size_t)nb * h->n_wave_words));
     CK(cudaStreamSynchronize(st));
     *out = h;
     return ACLZ_OK;
@@ -600,7 +659,7 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
 extern "C" int aclz_free(aclz_handle *h) {
     if (!h) return ACLZ_E_INVAL;
     void *ps[] = {h->d_tok, h->d_lit, h->d_blk_tok, h->d_blk_lit, h->d_slot, h->d_tokdst,
-                  h->d_tri, h->d_err, h->d_items, h->d_next, h->d_prog, h->d_ctr};
+                  h->d_tri, h->d_err, h->d_seg, h->d_ranges, h->d_pending, h->d_done};
     for (void *p : ps)
         if (p) cudaFree(p);
     delete h;
@@ -638,4 +697,40 @@ extern "C" int aclz_tags(const aclz_handle *h, uint32_t *host_tags, uint64_t cap
         return ACLZ_E_CUDA;
     for (uint64_t i = 0; i < h->n_tokens; i++) host_tags[i] = raw[4 * i + 3] >> 8;
     return ACLZ_OK;
+}
+
+extern "C" int aclz_set_range_bytes(aclz_handle *h, uint32_t range_bytes, void *stream) {
+    if (!h || range_bytes == 0) return ACLZ_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->range_bytes = range_bytes;
+    h->range_T = range_matches(range_bytes, h->mean_deferred_len);
+    if (h->d_ranges) {
+        cudaFree(h->d_ranges);
+        h->d_ranges = nullptr;
+    }
+    h->n_ranges = 0;
+    const uint64_t nseg = h->n_seg;
+    if (!nseg) return ACLZ_OK;
+    uint32_t *rflag = nullptr, *d_nr = nullptr;
+    if (cudaMalloc((void **)&rflag, 4 * (size_t)nseg + 16) != cudaSuccess) return ACLZ_E_NOMEM;
+    d_nr = rflag + nseg;
+    int rc = ACLZ_OK;
+    k_range_flags<<<1024, 256, 0, st>>>((const uint4 *)h->d_seg, nseg, h->range_T, rflag);
+    rc = device_excl_scan(rflag, nseg, d_nr, st);
+    uint32_t nr = 0;
+    if (rc == ACLZ_OK && cudaMemcpyAsync(&nr, d_nr, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = ACLZ_E_CUDA;
+    if (rc == ACLZ_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = ACLZ_E_CUDA;
+    if (rc == ACLZ_OK && nr) {
+        if (cudaMalloc(&h->d_ranges, 16 * ((size_t)nr + 1)) != cudaSuccess) {
+            rc = ACLZ_E_NOMEM;
+        } else {
+            h->n_ranges = nr;
+            k_range_build<<<1024, 256, 0, st>>>((const uint4 *)h->d_seg, rflag, nseg, nr,
+                                                 (uint32_t)h->n_deferred, (uint4 *)h->d_ranges);
+            if (cudaGetLastError() != cudaSuccess) rc = ACLZ_E_CUDA;
+            if (cudaStreamSynchronize(st) != cudaSuccess) rc = ACLZ_E_CUDA;
+        }
+    }
+    cudaFree(rflag);
+    return rc;
 }

@@ -52,6 +52,17 @@ struct View {
 // run on the device during upload.
 int parse_container(const uint8_t *c, uint64_t n, View *v, bool check_directory);
 
+// Remember the last CUDA runtime error for aclz_last_cuda_error().
+void note_cuda_error(int cuda_error_code);
+
+// Matches per work range for a target byte size of deferred matches.
+inline uint32_t range_matches(uint32_t range_bytes, double mean_len) {
+    double t = mean_len > 0 ? (double)range_bytes / mean_len : 16.0;
+    if (t < 8) t = 8;
+    if (t > 4096) t = 4096;
+    return (uint32_t)t;
+}
+
 }  // namespace aclz
 
 // Library handle: device copies of a container plus its decode index.
@@ -71,12 +82,21 @@ struct aclz_handle {
     void *d_tri = nullptr;        // n_deferred x 16 B triplets (decode scratch)
     uint32_t *d_err = nullptr;    // latched device status bits
     std::vector<uint64_t> wave_start;  // n_waves + 1 entries into the triplet array
-    // persistent-mode schedule: wave-major items, item i = {block, wave,
-    // triplet offset, triplet count}; items [0, n_blocks) are the wave-0
-    // block decodes, then one item per non-empty (wave, block) segment
-    void *d_items = nullptr;
-    uint32_t *d_next = nullptr;   // per item: the block's next non-empty wave
-    uint64_t n_items = 0;
-    uint32_t *d_prog = nullptr;   // per block: waves below this value are final
-    uint32_t *d_ctr = nullptr;    // reserved
+    // persistent-mode schedule.  A segment is the run of one block's
+    // matches in one wave's worklist: seg[s] = {block, wave, triplet offset,
+    // count}, wave-major then block order.  Items are [0, n_blocks) the
+    // wave-0 block decodes, then the ranges: runs of consecutive segments of
+    // one wave holding about range_T triplets, range[r] = {wave, first
+    // segment, end segment, 0}.
+    void *d_seg = nullptr;
+    void *d_ranges = nullptr;
+    uint64_t n_seg = 0, n_ranges = 0;
+    uint32_t range_T = 16;         // matches per range (from range_bytes / mean length)
+    uint32_t range_bytes = 16384;
+    double mean_deferred_len = 0;  // mean length of the deferred matches
+    // per block, n_wave_words 64-bit words: bit w of pending = block has work
+    // in wave w (bit 0 always); done = waves finished (empty waves preset)
+    uint32_t n_wave_words = 0;
+    uint64_t *d_pending = nullptr;
+    uint64_t *d_done = nullptr;
 };

@@ -20,13 +20,23 @@ def _lib():
     aclz.lib()  # raises if libaclz.so is missing: no fallback
 
 
-def gpu_decode(c, G=32, mode=aclz.ACLZ_MODE_WAVES, fnv=True):
+# (mode, flags): the wave schedule, and the persistent schedule with each
+# copy path
+WAVES = (aclz.ACLZ_MODE_WAVES, 0)
+PERSIST_STAGED = (aclz.ACLZ_MODE_PERSISTENT, aclz.ACLZ_FLAG_STAGED)
+PERSIST_REGS = (aclz.ACLZ_MODE_PERSISTENT, aclz.ACLZ_FLAG_REGISTERS)
+MODES = (WAVES, PERSIST_STAGED, PERSIST_REGS)
+
+
+def gpu_decode(c, G=32, mode=WAVES, fnv=True, range_bytes=None):
     s = torch.cuda.current_stream()
     h = aclz.aclz_upload(c, s)
     try:
         info = aclz.aclz_handle_info(h)
-        out = torch.empty(max(16, info.total_len), dtype=torch.uint8, device="cuda")
-        aclz.aclz_decode_all(h, out, G=G, mode=mode, stream=s)
+        if range_bytes:
+            aclz.aclz_set_range_bytes(h, range_bytes, s)
+        out = torch.empty(max(16, (info.total_len + 15) // 16 * 16), dtype=torch.uint8, device="cuda")
+        aclz.aclz_decode_all(h, out, G=G, mode=mode[0], flags=mode[1], stream=s)
         assert aclz.aclz_device_status(h, s) == aclz.ACLZ_OK
         got = out[:info.total_len].cpu().numpy()
         f = aclz.aclz_fnv(out, info.total_len, stream=s) if fnv else None
@@ -38,9 +48,6 @@ def gpu_decode(c, G=32, mode=aclz.ACLZ_MODE_WAVES, fnv=True):
 def h_info_dict(h):
     i = aclz.aclz_handle_info(h)
     return dict(n_waves=i.n_waves, n_deferred=i.n_deferred, n_tokens=i.n_tokens)
-
-
-MODES = (aclz.ACLZ_MODE_WAVES, aclz.ACLZ_MODE_PERSISTENT)
 
 
 def check(c, G=32, modes=MODES):
@@ -97,6 +104,21 @@ def test_wordtext_and_product_encoder():
         got, f, _ = gpu_decode(c, 16, mode)
         assert np.array_equal(got, x)
         assert f == oracle.fnv_chunked(x)
+
+
+@pytest.mark.parametrize("range_bytes", [64, 4096, 1 << 20])
+@pytest.mark.parametrize("mode", [PERSIST_STAGED, PERSIST_REGS])
+def test_persistent_range_sizes(range_bytes, mode):
+    """Ranges from 8 matches (more segments than lanes) to 4096 matches."""
+    x = synth.markov2(2 << 20, seed=17)
+    c = oracle.encode(x, 1 << 12, oracle.PRESET_BASE)
+    sw = synth.copy_sweep(4 << 20, 1 << 13, 512, seed=18)
+    c2 = oracle.pack_sweep(sw, tags=False)
+    for cc, G in ((c, 32), (c2, 8), (c2, 32)):
+        exp = oracle.decode(cc)
+        got, f, _ = gpu_decode(cc, G, mode, range_bytes=range_bytes)
+        assert np.array_equal(got, exp)
+        assert f == oracle.fnv_chunked(exp)
 
 
 # ------------------------------------------------------------ wave tags
