@@ -157,12 +157,13 @@ typedef struct aclz_decode_cfg {
 
 #define ACLZ_MODE_WAVES 0      /* wave 0, then one kernel per wave */
 #define ACLZ_MODE_PERSISTENT 1 /* wave 0, then one launch with bounded per-block waits */
+#define ACLZ_MODE_AUTO 2       /* persistent + staged when deferred matches average >= 192 B, else waves */
 #define ACLZ_FLAG_STAGED 1u    /* persistent: stage long matches through shared memory (TMA) */
 #define ACLZ_FLAG_REGISTERS 2u /* persistent: copy through registers only */
 
 /* Decode the whole stream into d_out (cap >= total_len bytes, 16-byte
  * aligned).  Enqueues on stream; capturable in a CUDA graph (no allocation,
- * no synchronization).  cfg NULL = {32, ACLZ_MODE_PERSISTENT, 0, 0}; the
+ * no synchronization).  cfg NULL = {32, ACLZ_MODE_AUTO, 0, 0}.  The
  * persistent mode stages long matches through shared memory when the
  * deferred matches average at least 192 bytes, unless a flag forces one
  * copy path. */

@@ -29,7 +29,7 @@ ACLZ_E_TIMEOUT = -6
 ACLZ_E_DEVICE = -7
 ACLZ_E_UNSUPPORTED = -8
 ACLZ_PRESET_BASE, ACLZ_PRESET_TUNED, ACLZ_PRESET_PUSH = 0, 1, 2
-ACLZ_MODE_WAVES, ACLZ_MODE_PERSISTENT = 0, 1
+ACLZ_MODE_WAVES, ACLZ_MODE_PERSISTENT, ACLZ_MODE_AUTO = 0, 1, 2
 ACLZ_FLAG_STAGED, ACLZ_FLAG_REGISTERS = 1, 2
 
 
@@ -239,7 +239,7 @@ def aclz_set_range_bytes(h: int, range_bytes: int, stream=None) -> None:
 
 
 def aclz_decode_all(h: int, d_out, cap: int | None = None, G: int = 32,
-                    mode: int = ACLZ_MODE_PERSISTENT, ctas_per_sm: int = 0, flags: int = 0,
+                    mode: int = ACLZ_MODE_AUTO, ctas_per_sm: int = 0, flags: int = 0,
                     stream=None) -> None:
     if cap is None:
         cap = int(d_out.numel() * d_out.element_size())

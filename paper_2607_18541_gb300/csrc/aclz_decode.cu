@@ -444,10 +444,17 @@ extern "C" int aclz_decode_all(aclz_handle *h, void *d_out, uint64_t cap, const 
     if (!h || (!d_out && h->total_len)) return ACLZ_E_INVAL;
     if (cap < h->total_len) return ACLZ_E_CAPACITY;
     if (reinterpret_cast<uintptr_t>(d_out) & 15) return ACLZ_E_INVAL;
-    aclz_decode_cfg c = {32, ACLZ_MODE_PERSISTENT, 0, 0};
+    aclz_decode_cfg c = {32, ACLZ_MODE_AUTO, 0, 0};
     if (cfg) c = *cfg;
     if (c.G != 8 && c.G != 16 && c.G != 32) return ACLZ_E_INVAL;
-    if (c.mode != ACLZ_MODE_WAVES && c.mode != ACLZ_MODE_PERSISTENT) return ACLZ_E_INVAL;
+    if (c.mode != ACLZ_MODE_WAVES && c.mode != ACLZ_MODE_PERSISTENT && c.mode != ACLZ_MODE_AUTO)
+        return ACLZ_E_INVAL;
+    if (c.mode == ACLZ_MODE_AUTO) {
+        // long deferred matches: one persistent launch with TMA staging;
+        // short ones: the per-wave kernels
+        c.mode = h->mean_deferred_len >= (double)kTmaMin ? ACLZ_MODE_PERSISTENT : ACLZ_MODE_WAVES;
+        if (c.mode == ACLZ_MODE_PERSISTENT && !(c.flags & ACLZ_FLAG_REGISTERS)) c.flags |= ACLZ_FLAG_STAGED;
+    }
     if ((c.flags & ACLZ_FLAG_STAGED) && (c.flags & ACLZ_FLAG_REGISTERS)) return ACLZ_E_INVAL;
     if (h->n_blocks == 0) return ACLZ_OK;
     cudaStream_t st = (cudaStream_t)stream;

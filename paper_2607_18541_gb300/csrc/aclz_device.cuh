@@ -185,6 +185,24 @@ __device__ __forceinline__ void group_copy(const Group<G> &g, uint8_t *out, uint
     }
 }
 
+// Bytes [r, r + 16) of a || b for a shift r that is the same on every lane
+// (a uniform branch picks the word offset).
+__device__ __forceinline__ uint4 window16_uniform(const uint4 &a, const uint4 &b, uint32_t q, uint32_t sh) {
+    uint32_t w0, w1, w2, w3, w4;
+    switch (q) {
+        case 0: w0 = a.x; w1 = a.y; w2 = a.z; w3 = a.w; w4 = b.x; break;
+        case 1: w0 = a.y; w1 = a.z; w2 = a.w; w3 = b.x; w4 = b.y; break;
+        case 2: w0 = a.z; w1 = a.w; w2 = b.x; w3 = b.y; w4 = b.z; break;
+        default: w0 = a.w; w1 = b.x; w2 = b.y; w3 = b.z; w4 = b.w; break;
+    }
+    uint4 o;
+    o.x = __funnelshift_r(w0, w1, sh);
+    o.y = __funnelshift_r(w1, w2, sh);
+    o.z = __funnelshift_r(w2, w3, sh);
+    o.w = __funnelshift_r(w3, w4, sh);
+    return o;
+}
+
 // ------------------------------------------------------- TMA staging
 
 // Per-group staging area for 1-D bulk copies (cp.async.bulk) from global
@@ -246,24 +264,6 @@ __device__ __forceinline__ bool stage_wait(Stage &st, uint32_t *err) {
     }
     st.phase ^= 1u;
     return ok;
-}
-
-// Bytes [r, r + 16) of a || b for a shift r that is the same on every lane
-// (a uniform branch picks the word offset).
-__device__ __forceinline__ uint4 window16_uniform(const uint4 &a, const uint4 &b, uint32_t q, uint32_t sh) {
-    uint32_t w0, w1, w2, w3, w4;
-    switch (q) {
-        case 0: w0 = a.x; w1 = a.y; w2 = a.z; w3 = a.w; w4 = b.x; break;
-        case 1: w0 = a.y; w1 = a.z; w2 = a.w; w3 = b.x; w4 = b.y; break;
-        case 2: w0 = a.z; w1 = a.w; w2 = b.x; w3 = b.y; w4 = b.z; break;
-        default: w0 = a.w; w1 = b.x; w2 = b.y; w3 = b.z; w4 = b.w; break;
-    }
-    uint4 o;
-    o.x = __funnelshift_r(w0, w1, sh);
-    o.y = __funnelshift_r(w1, w2, sh);
-    o.z = __funnelshift_r(w2, w3, sh);
-    o.w = __funnelshift_r(w3, w4, sh);
-    return o;
 }
 
 // Realign-and-store of one staged job: output [d, d + n) from the shared
