@@ -170,6 +170,26 @@ typedef struct aclz_decode_cfg {
 int aclz_decode_all(aclz_handle *h, void *d_out, uint64_t cap, const aclz_decode_cfg *cfg,
                     void *stream);
 
+/* Range decode (seek): write decode(stream)[lo, hi) to d_out (16-byte
+ * aligned, hi - lo bytes) without decoding the rest.  Absolute
+ * back-references let every output byte be traced back to the literal it
+ * copies (abstract; Sec. I: random access without whole-file
+ * decompression); only literals are read, never the output of other
+ * calls.  0 <= lo <= hi <= total_len, hi - lo < 4 GiB.  Enqueues on stream;
+ * no allocation. */
+int aclz_decode_range(aclz_handle *h, uint64_t lo, uint64_t hi, void *d_out, void *stream);
+
+/* Device scratch bytes that aclz_decode_ranges needs for n requests. */
+int aclz_ranges_scratch_bytes(uint32_t n_requests, uint64_t *out);
+
+/* Several range decodes in one launch: request i writes
+ * decode(stream)[host_lo[i], host_hi[i]) to host_out[i] (device pointers,
+ * 16-byte aligned).  The request table is copied to d_scratch
+ * (aclz_ranges_scratch_bytes) and the stream is synchronized once for that
+ * copy before the launch is enqueued. */
+int aclz_decode_ranges(aclz_handle *h, uint32_t n, const uint64_t *host_lo, const uint64_t *host_hi,
+                       void *const *host_out, void *d_scratch, uint64_t scratch_cap, void *stream);
+
 /* Synchronize stream and return the device status latched by decode
  * calls on h since the last call (ACLZ_OK, ACLZ_E_TIMEOUT, ACLZ_E_DEVICE). */
 int aclz_device_status(aclz_handle *h, void *stream);

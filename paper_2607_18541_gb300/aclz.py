@@ -82,6 +82,9 @@ _SIGS = [
     ("aclz_decode_all", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP]),
     ("aclz_device_status", _I, [_VP, _VP]),
     ("aclz_fnv", _I, [_VP, _U64, _U64P, _VP]),
+    ("aclz_decode_range", _I, [_VP, _U64, _U64, _VP, _VP]),
+    ("aclz_ranges_scratch_bytes", _I, [_U32, _U64P]),
+    ("aclz_decode_ranges", _I, [_VP, _U32, _U64P, _U64P, ctypes.POINTER(_VP), _VP, _U64, _VP]),
     ("aclz_strerror", ctypes.c_char_p, [_I]),
     ("aclz_last_cuda_error", _I, []),
 ]
@@ -249,6 +252,27 @@ def aclz_decode_all(h: int, d_out, cap: int | None = None, G: int = 32,
 
 def aclz_device_status(h: int, stream=None) -> int:
     return _ck(lib().aclz_device_status(h, _stream(stream)), "aclz_device_status")
+
+
+def aclz_decode_range(h: int, lo: int, hi: int, d_out, stream=None) -> None:
+    _ck(lib().aclz_decode_range(h, lo, hi, _dptr(d_out), _stream(stream)), "aclz_decode_range")
+
+
+def aclz_ranges_scratch_bytes(n_requests: int) -> int:
+    out = ctypes.c_uint64(0)
+    _ck(lib().aclz_ranges_scratch_bytes(n_requests, ctypes.byref(out)), "aclz_ranges_scratch_bytes")
+    return int(out.value)
+
+
+def aclz_decode_ranges(h: int, lo, hi, outs, d_scratch, scratch_cap: int | None = None, stream=None) -> None:
+    n = len(lo)
+    lo_a = np.ascontiguousarray(lo, dtype=np.uint64)
+    hi_a = np.ascontiguousarray(hi, dtype=np.uint64)
+    ptrs = (_VP * max(1, n))(*[_dptr(o) for o in outs])
+    if scratch_cap is None:
+        scratch_cap = int(d_scratch.numel() * d_scratch.element_size())
+    _ck(lib().aclz_decode_ranges(h, n, lo_a.ctypes.data_as(_U64P), hi_a.ctypes.data_as(_U64P), ptrs,
+                                 _dptr(d_scratch), scratch_cap, _stream(stream)), "aclz_decode_ranges")
 
 
 def aclz_fnv(d_buf, n: int | None = None, stream=None) -> int:

@@ -38,7 +38,8 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
 __global__ void __launch_bounds__(256) k_index_scan(const uint4 *__restrict__ tok,
                                                     const uint64_t *__restrict__ blk_tok,
                                                     const uint64_t *__restrict__ blk_lit,
-                                                    uint32_t *__restrict__ tokdst, uint32_t nb,
+                                                    uint32_t *__restrict__ tokdst,
+                                                    uint32_t *__restrict__ toklit, uint32_t nb,
                                                     uint32_t log2bs, uint64_t total, int has_tags,
                                                     uint32_t *err, unsigned long long *first_bad) {
     Group<32> g;
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(256) k_index_scan(const uint4 *__restrict__ to
                 atomicMin(first_bad, (unsigned long long)i);
             }
             tokdst[i] = (uint32_t)rel;
+            toklit[i] = (uint32_t)(lcarry + lsum - lit);
         }
         carry += g.shfl(incl, 31);
         lcarry += g.shfl(lsum, 31);
@@ -521,6 +523,7 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
     CK(cudaMalloc((void **)&h->d_blk_tok, 8 * (nb + 1)));
     CK(cudaMalloc((void **)&h->d_blk_lit, 8 * (nb + 1)));
     CK(cudaMalloc((void **)&h->d_tokdst, 4 * (nt ? nt : 1)));
+    CK(cudaMalloc((void **)&h->d_toklit, 4 * (nt ? nt : 1)));
     CK(cudaMalloc((void **)&h->d_slot, 4 * (nt ? nt : 1)));
     CK(cudaMalloc((void **)&h->d_err, 64));
     CK(cudaMemsetAsync(h->d_err, 0, 64, st));
@@ -548,7 +551,7 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
     const unsigned wblocks = (nb + 7) / 8;  // 8 warps per CTA
     const bool has_tags = (v.flags & kFlagWaves) != 0;
     k_index_scan<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_blk_lit,
-                                           h->d_tokdst, nb, h->log2_bs, v.total_len, has_tags,
+                                           h->d_tokdst, h->d_toklit, nb, h->log2_bs, v.total_len, has_tags,
                                            h->d_err, d_first_bad);
     CK(cudaGetLastError());
     uint32_t herr = 0;
@@ -658,7 +661,7 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
 
 extern "C" int aclz_free(aclz_handle *h) {
     if (!h) return ACLZ_E_INVAL;
-    void *ps[] = {h->d_tok, h->d_lit, h->d_blk_tok, h->d_blk_lit, h->d_slot, h->d_tokdst,
+    void *ps[] = {h->d_tok, h->d_lit, h->d_blk_tok, h->d_blk_lit, h->d_slot, h->d_tokdst, h->d_toklit,
                   h->d_tri, h->d_err, h->d_seg, h->d_ranges, h->d_pending, h->d_done};
     for (void *p : ps)
         if (p) cudaFree(p);

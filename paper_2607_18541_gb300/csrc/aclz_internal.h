@@ -79,6 +79,7 @@ struct aclz_handle {
     uint64_t *d_blk_lit = nullptr;  // n_blocks + 1 literal offsets
     uint32_t *d_slot = nullptr;   // per token: triplet slot of a deferred match, else ~0u
     uint32_t *d_tokdst = nullptr; // per token: block-relative offset of its first byte
+    uint32_t *d_toklit = nullptr; // per token: block-relative offset of its first literal
     void *d_tri = nullptr;        // n_deferred x 16 B triplets (decode scratch)
     uint32_t *d_err = nullptr;    // latched device status bits
     std::vector<uint64_t> wave_start;  // n_waves + 1 entries into the triplet array
