@@ -190,6 +190,26 @@ int aclz_ranges_scratch_bytes(uint32_t n_requests, uint64_t *out);
 int aclz_decode_ranges(aclz_handle *h, uint32_t n, const uint64_t *host_lo, const uint64_t *host_hi,
                        void *const *host_out, void *d_scratch, uint64_t scratch_cap, void *stream);
 
+/* Batched decode (many independent streams in one launch): merge n host
+ * containers of one block size into one container whose stream i starts
+ * on a block boundary at *out_offsets[i]; its sources are rebased by that
+ * offset (streams never reference one another) and its last block is
+ * padded with zero literals up to the block size.  Decoding the merged
+ * container writes stream i to [out_offsets[i], out_offsets[i] +
+ * total_len_i).  host_out NULL: only *out_size (the size needed) and the
+ * offsets are computed.  Wave tags are kept when every input has them. */
+int aclz_batch_merge(uint32_t n, const void *const *host_bufs, const uint64_t *sizes, void *host_out,
+                     uint64_t cap, uint64_t *out_size, uint64_t *out_offsets);
+
+/* CUDA graph of one aclz_decode_all(h, d_out, cap, cfg) call, captured on
+ * a private stream after one plain decode on `stream` (which it
+ * synchronizes).  Launching the graph repeats the whole decode. */
+typedef struct aclz_graph aclz_graph;
+int aclz_graph_create(aclz_handle *h, void *d_out, uint64_t cap, const aclz_decode_cfg *cfg, void *stream,
+                      aclz_graph **out);
+int aclz_graph_launch(aclz_graph *g, void *stream);
+int aclz_graph_free(aclz_graph *g);
+
 /* Synchronize stream and return the device status latched by decode
  * calls on h since the last call (ACLZ_OK, ACLZ_E_TIMEOUT, ACLZ_E_DEVICE). */
 int aclz_device_status(aclz_handle *h, void *stream);

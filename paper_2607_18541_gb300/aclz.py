@@ -85,6 +85,10 @@ _SIGS = [
     ("aclz_decode_range", _I, [_VP, _U64, _U64, _VP, _VP]),
     ("aclz_ranges_scratch_bytes", _I, [_U32, _U64P]),
     ("aclz_decode_ranges", _I, [_VP, _U32, _U64P, _U64P, ctypes.POINTER(_VP), _VP, _U64, _VP]),
+    ("aclz_batch_merge", _I, [_U32, ctypes.POINTER(_VP), _U64P, _VP, _U64, _U64P, _U64P]),
+    ("aclz_graph_create", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP, ctypes.POINTER(_VP)]),
+    ("aclz_graph_launch", _I, [_VP, _VP]),
+    ("aclz_graph_free", _I, [_VP]),
     ("aclz_strerror", ctypes.c_char_p, [_I]),
     ("aclz_last_cuda_error", _I, []),
 ]
@@ -273,6 +277,42 @@ def aclz_decode_ranges(h: int, lo, hi, outs, d_scratch, scratch_cap: int | None 
         scratch_cap = int(d_scratch.numel() * d_scratch.element_size())
     _ck(lib().aclz_decode_ranges(h, n, lo_a.ctypes.data_as(_U64P), hi_a.ctypes.data_as(_U64P), ptrs,
                                  _dptr(d_scratch), scratch_cap, _stream(stream)), "aclz_decode_ranges")
+
+
+def aclz_batch_merge(containers):
+    """Returns (merged container, per-stream output offsets)."""
+    arrs = [_np_u8(c) for c in containers]
+    n = len(arrs)
+    ptrs = (_VP * n)(*[_hptr(a) if a.size else None for a in arrs])
+    sizes = np.array([a.size for a in arrs], dtype=np.uint64)
+    offs = np.zeros(n, dtype=np.uint64)
+    need = ctypes.c_uint64(0)
+    _ck(lib().aclz_batch_merge(n, ptrs, sizes.ctypes.data_as(_U64P), None, 0, ctypes.byref(need),
+                               offs.ctypes.data_as(_U64P)), "aclz_batch_merge")
+    out = np.empty(need.value, dtype=np.uint8)
+    size = ctypes.c_uint64(0)
+    _ck(lib().aclz_batch_merge(n, ptrs, sizes.ctypes.data_as(_U64P), _hptr(out), out.size, ctypes.byref(size),
+                               offs.ctypes.data_as(_U64P)), "aclz_batch_merge")
+    return out[:size.value], offs
+
+
+def aclz_graph_create(h: int, d_out, cap: int | None = None, G: int = 32, mode: int = ACLZ_MODE_AUTO,
+                      ctas_per_sm: int = 0, flags: int = 0, stream=None) -> int:
+    if cap is None:
+        cap = int(d_out.numel() * d_out.element_size())
+    cfg = aclz_decode_cfg(G, mode, ctas_per_sm, flags)
+    g = ctypes.c_void_p(0)
+    _ck(lib().aclz_graph_create(h, _dptr(d_out), cap, ctypes.byref(cfg), _stream(stream), ctypes.byref(g)),
+        "aclz_graph_create")
+    return int(g.value)
+
+
+def aclz_graph_launch(g: int, stream=None) -> None:
+    _ck(lib().aclz_graph_launch(g, _stream(stream)), "aclz_graph_launch")
+
+
+def aclz_graph_free(g: int) -> None:
+    _ck(lib().aclz_graph_free(g), "aclz_graph_free")
 
 
 def aclz_fnv(d_buf, n: int | None = None, stream=None) -> int:

@@ -487,3 +487,58 @@ extern "C" int aclz_device_status(aclz_handle *h, void *stream) {
     if (e) return ACLZ_E_DEVICE;
     return ACLZ_OK;
 }
+
+// ------------------------------------------------------------- graphs
+
+struct aclz_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" int aclz_graph_create(aclz_handle *h, void *d_out, uint64_t cap, const aclz_decode_cfg *cfg,
+                                 void *stream, aclz_graph **out) {
+    if (!h || !out) return ACLZ_E_INVAL;
+    *out = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    // one plain decode first: sets kernel attributes and occupancy caches
+    int rc = aclz_decode_all(h, d_out, cap, cfg, stream);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return ACLZ_E_CUDA;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return ACLZ_E_CUDA;
+    aclz_graph *g = new aclz_graph();
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = aclz_decode_all(h, d_out, cap, cfg, cs);
+        e = cudaStreamEndCapture(cs, &g->graph);
+        if (e == cudaSuccess && rc == ACLZ_OK) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess || rc != ACLZ_OK) {
+        if (e != cudaSuccess) note_cuda_error(e);
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return rc ? rc : ACLZ_E_CUDA;
+    }
+    *out = g;
+    return ACLZ_OK;
+}
+
+extern "C" int aclz_graph_launch(aclz_graph *g, void *stream) {
+    if (!g) return ACLZ_E_INVAL;
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        return ACLZ_E_CUDA;
+    }
+    return ACLZ_OK;
+}
+
+extern "C" int aclz_graph_free(aclz_graph *g) {
+    if (!g) return ACLZ_E_INVAL;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return ACLZ_OK;
+}

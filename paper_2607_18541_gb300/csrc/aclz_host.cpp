@@ -361,6 +361,101 @@ int aclz_encode(const void *host_src, uint64_t n, const aclz_encode_params *p,
     return ACLZ_OK;
 }
 
+int aclz_batch_merge(uint32_t n, const void *const *host_bufs, const uint64_t *sizes, void *host_out,
+                     uint64_t cap, uint64_t *out_size, uint64_t *out_offsets) {
+    if (n == 0 || !host_bufs || !sizes || !out_size || !out_offsets) return ACLZ_E_INVAL;
+    std::vector<View> vs(n);
+    uint32_t bs = 0;
+    bool all_tags = true;
+    uint32_t max_waves = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        int rc = parse_container((const uint8_t *)host_bufs[i], sizes[i], &vs[i], true);
+        if (rc) return rc;
+        if (i == 0) bs = vs[i].block_size;
+        if (vs[i].block_size != bs) return ACLZ_E_INVAL;
+        if (!(vs[i].flags & kFlagWaves)) all_tags = false;
+        max_waves = std::max(max_waves, vs[i].n_waves);
+    }
+    // sizes of the merged container
+    uint64_t total = 0, nt = 0, nl = 0, nb = 0;
+    std::vector<uint64_t> pad(n, 0);
+    for (uint32_t i = 0; i < n; i++) {
+        const View &v = vs[i];
+        out_offsets[i] = total;
+        if (v.total_len == 0) continue;
+        pad[i] = (i + 1 < n && v.total_len % bs) ? bs - v.total_len % bs : 0;
+        total += v.total_len + pad[i];
+        nb += v.n_blocks;
+        nt += v.n_tokens;
+        nl += v.n_literals + pad[i];
+        if (pad[i]) {
+            // a padded block ending in a match gets one more token
+            const uint8_t *last = v.tok + (uint64_t)kTok * (v.n_tokens - 1);
+            if (rd32(last + 4) != 0) nt++;
+        }
+    }
+    if (total > kSrcMask || nb > 0xffffffffULL) return ACLZ_E_UNSUPPORTED;
+    const uint64_t need = aclz_pack_bytes(total, bs, nt, nl);
+    if (!host_out) { *out_size = need; return ACLZ_OK; }
+    if (cap < need) return ACLZ_E_CAPACITY;
+    uint8_t *c = (uint8_t *)host_out;
+    write_header(c, total, bs, (uint32_t)nb, nt, nl, vs[0].mm);
+    uint8_t *dir = c + kHdr, *tok = dir + (uint64_t)kDirent * nb, *lit = tok + (uint64_t)kTok * nt;
+    uint64_t b = 0, t = 0, l = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        const View &v = vs[i];
+        if (v.total_len == 0) continue;
+        const uint64_t base = out_offsets[i];
+        for (uint32_t k = 0; k < v.n_blocks; k++, b++) {
+            const uint8_t *d = v.dir + (uint64_t)kDirent * k;
+            uint8_t *o = dir + (uint64_t)kDirent * b;
+            std::memcpy(o, d, kDirent);
+            wr64(o, t);
+            wr64(o + 8, l);
+            const uint64_t t0 = rd64(d);
+            uint32_t ntok = rd32(d + 16);
+            const bool last_block = k + 1 == v.n_blocks;
+            for (uint32_t j = 0; j < ntok; j++) {
+                const uint8_t *src = v.tok + (uint64_t)kTok * (t0 + j);
+                uint8_t *dt = tok + (uint64_t)kTok * t;
+                std::memcpy(dt, src, kTok);
+                const uint64_t sw = rd64(src + 8);
+                if (rd32(src + 4)) wr64(dt + 8, ((sw & kSrcMask) + base) | (all_tags ? (sw & ~kSrcMask) : 0));
+                else if (!all_tags) wr64(dt + 8, 0);
+                t++;
+            }
+            // literal bytes of the block, in token order
+            const uint64_t l0 = rd64(d + 8);
+            const uint64_t l1 = k + 1 < v.n_blocks ? rd64(d + kDirent + 8) : v.n_literals;
+            std::memcpy(lit + l, v.lit + l0, l1 - l0);
+            l += l1 - l0;
+            if (last_block && pad[i]) {
+                uint8_t *lt = tok + (uint64_t)kTok * (t - 1);
+                if (rd32(lt + 4) == 0) {
+                    wr32(lt, rd32(lt) + (uint32_t)pad[i]);
+                } else {
+                    uint8_t *dt = tok + (uint64_t)kTok * t;
+                    wr32(dt, (uint32_t)pad[i]);
+                    wr32(dt + 4, 0);
+                    wr64(dt + 8, 0);
+                    t++;
+                    ntok++;
+                }
+                std::memset(lit + l, 0, pad[i]);
+                l += pad[i];
+            }
+            wr32(o + 16, ntok);
+            if (!all_tags) wr16(o + 20, 0);
+        }
+    }
+    if (all_tags) {
+        wr16(c + 6, kFlagWaves);
+        wr32(c + 40, nt ? std::max<uint32_t>(max_waves, 1) : 0);
+    }
+    *out_size = need;
+    return (b == nb && t == nt && l == nl) ? ACLZ_OK : ACLZ_E_CORRUPT;
+}
+
 int aclz_container_info(const void *host_buf, uint64_t n, aclz_info *out) {
     if (!host_buf || !out) return ACLZ_E_INVAL;
     View v;

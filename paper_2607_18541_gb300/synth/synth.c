@@ -178,19 +178,45 @@ static int draw_cum32(synth_rng *r, const uint64_t *cum, int n) {
 /* ============================================= order-2 Markov byte stream */
 
 /* Model: 64 symbols 0x30..0x6F; each of the 64*64 contexts draws its
- * next-symbol distribution from Dirichlet(alpha). */
+ * next-symbol distribution from Dirichlet(alpha), stored as an alias table
+ * (Vose's method): draw column i uniformly, keep it with probability
+ * prob[i] / 2^32, else take alias[i]. */
+typedef struct {
+    uint32_t prob[4096][64];
+    uint8_t alias[4096][64];
+} markov_model;
+
+static void alias_build(const double *w, int n, uint32_t *prob, uint8_t *alias) {
+    double tot = 0.0, q[64];
+    int small[64], large[64], ns = 0, nl = 0;
+    for (int i = 0; i < n; i++) tot += w[i];
+    for (int i = 0; i < n; i++) {
+        q[i] = w[i] / tot * (double)n;
+        if (q[i] < 1.0) small[ns++] = i; else large[nl++] = i;
+    }
+    while (ns && nl) {
+        int s1 = small[--ns], l1 = large[nl - 1];
+        prob[s1] = (uint32_t)(q[s1] * 4294967296.0 > 4294967295.0 ? 4294967295.0 : q[s1] * 4294967296.0);
+        alias[s1] = (uint8_t)l1;
+        q[l1] = (q[l1] + q[s1]) - 1.0;
+        if (q[l1] < 1.0) { nl--; small[ns++] = l1; }
+    }
+    while (nl) { int l1 = large[--nl]; prob[l1] = 0xffffffffu; alias[l1] = (uint8_t)l1; }
+    while (ns) { int s1 = small[--ns]; prob[s1] = 0xffffffffu; alias[s1] = (uint8_t)s1; }
+}
+
 void *synth_markov_model_new(uint64_t model_seed, double alpha) {
     if (!(alpha > 0.0)) return NULL;
-    uint64_t *cum = (uint64_t *)malloc(sizeof(uint64_t) * 4096 * 64);
-    if (!cum) return NULL;
+    markov_model *m = (markov_model *)malloc(sizeof(markov_model));
+    if (!m) return NULL;
     synth_rng r;
     rng_seed(&r, model_seed);
     double w[64];
     for (int c = 0; c < 4096; c++) {
         for (int i = 0; i < 64; i++) w[i] = gamma_draw(&r, alpha);
-        weights_to_cum32(w, 64, cum + (size_t)c * 64);
+        alias_build(w, 64, m->prob[c], m->alias[c]);
     }
-    return cum;
+    return m;
 }
 
 void synth_markov_model_free(void *m) { free(m); }
@@ -202,7 +228,7 @@ void synth_markov_model_free(void *m) { free(m); }
 int synth_markov2_gen(const void *model, uint8_t *out, uint64_t n, uint64_t seed,
                       uint32_t repeat_every, uint32_t repeat_mean) {
     if (!model || (!out && n) || repeat_every == 0 || repeat_mean == 0) return SYNTH_E_INVAL;
-    const uint64_t *cum = (const uint64_t *)model;
+    const markov_model *m = (const markov_model *)model;
     synth_rng r;
     rng_seed(&r, seed ^ 0x3a4b5c6d7e8f9012ULL);
     int s1 = (int)rng_below(&r, 64), s2 = (int)rng_below(&r, 64);
@@ -220,7 +246,10 @@ int synth_markov2_gen(const void *model, uint8_t *out, uint64_t n, uint64_t seed
                 continue;
             }
         }
-        int s = draw_cum32(&r, cum + (size_t)(s1 * 64 + s2) * 64, 64);
+        const int c = s1 * 64 + s2;
+        const uint64_t x = rng_next(&r);
+        const int col = (int)(x >> 58);
+        const int s = ((uint32_t)x < m->prob[c][col]) ? col : m->alias[c][col];
         out[pos++] = (uint8_t)(0x30 + s);
         s1 = s2;
         s2 = s;

@@ -1,0 +1,67 @@
+"""Batched decode (one persistent launch over many merged streams, graph
+captured) against the original stream bytes and the single-stream decode."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_18541_gb300 import aclz, batched, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    aclz.lib()
+
+
+@pytest.mark.parametrize("mode", ["auto", "persistent", "waves"])
+def test_batched_equals_streams_and_single_stream_decode(mode):
+    streams = batched.make_streams(48, 16 << 10, 1 << 20, seed=123)
+    p = aclz.aclz_encode_params_default(aclz.ACLZ_PRESET_TUNED)
+    p.block_size = 1 << 13
+    cs = batched.encode_streams(streams, p)
+    cfg = {"auto": {}, "persistent": dict(mode=aclz.ACLZ_MODE_PERSISTENT, flags=aclz.ACLZ_FLAG_STAGED),
+           "waves": dict(mode=aclz.ACLZ_MODE_WAVES)}[mode]
+    s = torch.cuda.current_stream()
+    dec = batched.BatchDecoder(cs, stream=s)
+    try:
+        dec.decode(**cfg)
+        assert aclz.aclz_device_status(dec.h, s) == 0
+        for i, x in enumerate(streams):
+            assert np.array_equal(dec.stream_output(i).cpu().numpy(), x), i
+        # graph replay gives the same bytes
+        dec.out.zero_()
+        dec.capture(**cfg)
+        dec.replay()
+        dec.replay()
+        assert aclz.aclz_device_status(dec.h, s) == 0
+        for i, x in enumerate(streams):
+            assert np.array_equal(dec.stream_output(i).cpu().numpy(), x), i
+        # each stream alone (single-stream decode) equals its slice of the batch
+        ms, outs = batched.time_one_by_one(cs[:8], stream=s, reps=1, **cfg)
+        for i in range(8):
+            n = streams[i].size
+            assert torch.equal(outs[i][:n], dec.stream_output(i))
+    finally:
+        dec.close()
+
+
+def test_merged_oracle_tags_are_kept_and_decoded():
+    xs = [synth.fastq(n, seed=i) for i, n in enumerate((5000, 80000, 33333))]
+    cs = [oracle.encode(x, 4096, oracle.PRESET_BASE) for x in xs]
+    merged, offs = aclz.aclz_batch_merge(cs)
+    assert oracle.header(merged).flags == 1 and oracle.validate(merged) == 0
+    s = torch.cuda.current_stream()
+    h = aclz.aclz_upload(merged, s)
+    try:
+        n = aclz.aclz_handle_info(h).total_len
+        out = torch.empty((n + 15) // 16 * 16, dtype=torch.uint8, device="cuda")
+        aclz.aclz_decode_all(h, out, stream=s)
+        got = out.cpu().numpy()
+        for x, o in zip(xs, offs):
+            assert np.array_equal(got[int(o):int(o) + x.size], x)
+    finally:
+        aclz.aclz_free(h)

@@ -113,3 +113,31 @@ def test_container_info_and_argument_errors():
     assert e.value.code == aclz.ACLZ_E_CORRUPT
     with pytest.raises(aclz.AclzError):
         aclz.aclz_encode_params_default(7)
+
+
+def test_batch_merge_matches_oracle_decode():
+    xs = [synth.markov2(n, seed=i)[:n] if n else np.zeros(0, np.uint8)
+          for i, n in enumerate((1000, 70000, 0, 65536, 123457))]
+    cs = [oracle.encode(x, 4096, oracle.PRESET_BASE) for x in xs]
+    merged, offs = aclz.aclz_batch_merge(cs)
+    assert oracle.validate(merged) == 0
+    full = oracle.decode(merged)
+    for x, o in zip(xs, offs):
+        assert int(o) % 4096 == 0
+        assert np.array_equal(full[int(o):int(o) + x.size], x)
+    stripped, _ = aclz.aclz_batch_merge([oracle.strip_tags(c) for c in cs])
+    assert oracle.header(stripped).flags == 0
+    assert np.array_equal(oracle.decode(stripped), full)
+
+
+def test_lanes_law_follows_table_one():
+    # Table I: normalised throughput 0.31 at 32K lanes, ~0.52 at 65K,
+    # ~0.8 at 131K, 1.0 at >= 1M lanes
+    from paper_2607_18541_gb300 import autotune
+    assert abs(autotune.lanes_law(32_768) - 0.31) < 1e-9
+    assert abs(autotune.lanes_law(65_536) - 0.525) < 1e-9
+    assert abs(autotune.lanes_law(131_072) - 0.81) < 1e-9
+    assert autotune.lanes_law(1 << 20) == 1.0 and autotune.lanes_law(1 << 24) == 1.0
+    xs = [1 << k for k in range(10, 24)]
+    vals = [autotune.lanes_law(x) for x in xs]
+    assert all(b >= a for a, b in zip(vals, vals[1:]))
