@@ -190,6 +190,21 @@ int aclz_ranges_scratch_bytes(uint32_t n_requests, uint64_t *out);
 int aclz_decode_ranges(aclz_handle *h, uint32_t n, const uint64_t *host_lo, const uint64_t *host_hi,
                        void *const *host_out, void *d_scratch, uint64_t scratch_cap, void *stream);
 
+/* One range request for aclz_decode_ranges_async: decode(stream)[lo, hi)
+ * into d_out (device, 16-byte aligned); seg_base is filled in by the call. */
+typedef struct aclz_range_req {
+    uint64_t lo, hi;
+    void *d_out;
+    uint64_t seg_base;
+} aclz_range_req;
+
+/* Like aclz_decode_ranges without any copy or synchronization: reqs must
+ * be host memory the device can read (pinned, e.g. cudaHostAlloc) and must
+ * stay allocated and unchanged until the launch has completed on stream;
+ * the kernel reads the table from there.  For serving loops that overlap
+ * many batches. */
+int aclz_decode_ranges_async(aclz_handle *h, uint32_t n, aclz_range_req *reqs, void *stream);
+
 /* Batched decode (many independent streams in one launch): merge n host
  * containers of one block size into one container whose stream i starts
  * on a block boundary at *out_offsets[i]; its sources are rebased by that

@@ -56,6 +56,11 @@ class aclz_info(ctypes.Structure):
                 ("min_match", ctypes.c_uint8 * 4), ("reserved", ctypes.c_uint32)]
 
 
+class aclz_range_req(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_uint64), ("d_out", ctypes.c_void_p),
+                ("seg_base", ctypes.c_uint64)]
+
+
 class aclz_decode_cfg(ctypes.Structure):
     _fields_ = [("G", ctypes.c_uint32), ("mode", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
@@ -85,6 +90,7 @@ _SIGS = [
     ("aclz_decode_range", _I, [_VP, _U64, _U64, _VP, _VP]),
     ("aclz_ranges_scratch_bytes", _I, [_U32, _U64P]),
     ("aclz_decode_ranges", _I, [_VP, _U32, _U64P, _U64P, ctypes.POINTER(_VP), _VP, _U64, _VP]),
+    ("aclz_decode_ranges_async", _I, [_VP, _U32, _VP, _VP]),
     ("aclz_batch_merge", _I, [_U32, ctypes.POINTER(_VP), _U64P, _VP, _U64, _U64P, _U64P]),
     ("aclz_graph_create", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP, ctypes.POINTER(_VP)]),
     ("aclz_graph_launch", _I, [_VP, _VP]),
@@ -277,6 +283,12 @@ def aclz_decode_ranges(h: int, lo, hi, outs, d_scratch, scratch_cap: int | None 
         scratch_cap = int(d_scratch.numel() * d_scratch.element_size())
     _ck(lib().aclz_decode_ranges(h, n, lo_a.ctypes.data_as(_U64P), hi_a.ctypes.data_as(_U64P), ptrs,
                                  _dptr(d_scratch), scratch_cap, _stream(stream)), "aclz_decode_ranges")
+
+
+def aclz_decode_ranges_async(h: int, n: int, reqs_ptr: int, stream=None) -> None:
+    """reqs_ptr: address of n aclz_range_req in pinned host memory (32 B each:
+    lo, hi, d_out, seg_base), kept alive until the launch completes."""
+    _ck(lib().aclz_decode_ranges_async(h, n, reqs_ptr, _stream(stream)), "aclz_decode_ranges_async")
 
 
 def aclz_batch_merge(containers):

@@ -244,3 +244,22 @@ extern "C" int aclz_decode_ranges(aclz_handle *h, uint32_t n, const uint64_t *ho
     if (cudaStreamSynchronize(st) != cudaSuccess) return ACLZ_E_CUDA;
     return seek_launch(h, (const SeekReq *)d_scratch, rq[0], n, nseg, st);
 }
+
+extern "C" int aclz_decode_ranges_async(aclz_handle *h, uint32_t n, aclz_range_req *reqs, void *stream) {
+    static_assert(sizeof(aclz_range_req) == sizeof(SeekReq), "request layout");
+    if (!h || (n && !reqs)) return ACLZ_E_INVAL;
+    if (n == 0) return ACLZ_OK;
+    uint64_t nseg = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        aclz_range_req &r = reqs[i];
+        if (r.lo > r.hi || r.hi > h->total_len) return ACLZ_E_INVAL;
+        if (r.hi - r.lo >= (1ULL << 32)) return ACLZ_E_UNSUPPORTED;
+        if (r.hi > r.lo && (!r.d_out || (reinterpret_cast<uintptr_t>(r.d_out) & 15))) return ACLZ_E_INVAL;
+        r.seg_base = nseg;
+        nseg += (r.hi - r.lo + kSeg0 - 1) / kSeg0;
+    }
+    const SeekReq *dev = reinterpret_cast<const SeekReq *>(reqs);
+    SeekReq first;
+    std::memcpy(&first, reqs, sizeof(first));
+    return seek_launch(h, dev, first, n, nseg, (cudaStream_t)stream);
+}
