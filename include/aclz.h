@@ -170,6 +170,23 @@ typedef struct aclz_decode_cfg {
 int aclz_decode_all(aclz_handle *h, void *d_out, uint64_t cap, const aclz_decode_cfg *cfg,
                     void *stream);
 
+/* aclz_decode_all that also records phase_event (a cudaEvent_t owned by the
+ * caller) on stream between its two phases: after the wave-0 kernel
+ * (literals and in-order matches, Sec. III-B) and before the deferred
+ * matches of waves >= 1.  With its own events before and after the call a
+ * caller times each phase on the launching stream.  phase_event NULL is
+ * aclz_decode_all; a failed record is reported by the next CUDA call. */
+int aclz_decode_all_ev(aclz_handle *h, void *d_out, uint64_t cap, const aclz_decode_cfg *cfg,
+                       void *stream, void *phase_event);
+
+/* What aclz_decode_all would launch for this handle and cfg (no GPU work):
+ * *resolved = cfg with ACLZ_MODE_AUTO resolved and the copy-path flag set;
+ * *launches = kernel launches of one call (wave 0, then one persistent
+ * launch or one per non-empty wave >= 1; 0 for an empty stream).  Either
+ * output may be NULL.  ACLZ_E_INVAL for a bad cfg, as aclz_decode_all. */
+int aclz_decode_plan(const aclz_handle *h, const aclz_decode_cfg *cfg, aclz_decode_cfg *resolved,
+                     uint32_t *launches);
+
 /* Range decode (seek): write decode(stream)[lo, hi) to d_out (16-byte
  * aligned, hi - lo bytes) without decoding the rest.  Absolute
  * back-references let every output byte be traced back to the literal it
@@ -224,6 +241,39 @@ int aclz_graph_create(aclz_handle *h, void *d_out, uint64_t cap, const aclz_deco
                       aclz_graph **out);
 int aclz_graph_launch(aclz_graph *g, void *stream);
 int aclz_graph_free(aclz_graph *g);
+
+/* ---- learned per-block thresholds (no counterpart in the paper's
+ * decoder; the paper's lever, Sec. IV-B/IV-C, is a fixed vector of minimum
+ * match lengths by distance class, and the network chooses one of K such
+ * vectors per block).  FP32 MLP 24 -> 64 -> 64 -> K (2 <= K <= 16), ReLU,
+ * parameters one flat device array in the order W1[24][64], b1[64],
+ * W2[64][64], b2[64], W3[64][K], b3[K] (row-major). */
+uint32_t aclz_mlp_param_count(uint32_t K);
+
+/* Bytes of scratch aclz_mlp_grad needs for a batch. */
+uint64_t aclz_mlp_scratch_bytes(uint32_t K, uint32_t batch);
+
+/* logits[batch][K] = MLP(x[batch][24]). */
+int aclz_mlp_forward(const float *d_params, uint32_t K, const float *d_x, uint32_t batch, float *d_logits,
+                     void *stream);
+
+/* Mean softmax cross-entropy of labels y (0 <= y < K) and its gradient
+ * with respect to every parameter (d_grad, param_count floats; *d_loss one
+ * float, may be NULL).  Per-tile partials are summed in a fixed order. */
+int aclz_mlp_grad(const float *d_params, uint32_t K, const float *d_x, const int32_t *d_y, uint32_t batch,
+                  float *d_grad, float *d_loss, void *d_scratch, uint64_t scratch_bytes, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; step
+ * counts from 1) on d_params with moments d_m, d_v. */
+int aclz_mlp_adam(float *d_params, float *d_m, float *d_v, const float *d_grad, uint32_t K, uint32_t step,
+                  float lr, void *stream);
+
+/* Ten byte statistics per block of block_size bytes of d_x (n bytes):
+ * order-0 entropy / 8, distinct byte values / 256, fraction of bytes equal
+ * to the previous one, 4-gram and 8-gram repeat rates (linear counting over
+ * a 65536-bit hash map), fractions of digits, lowercase, uppercase,
+ * space/punctuation and other bytes.  d_feat: [n_blocks][10] floats. */
+int aclz_block_features(const void *d_x, uint64_t n, uint32_t block_size, float *d_feat, void *stream);
 
 /* Synchronize stream and return the device status latched by decode
  * calls on h since the last call (ACLZ_OK, ACLZ_E_TIMEOUT, ACLZ_E_DEVICE). */

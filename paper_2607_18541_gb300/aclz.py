@@ -85,6 +85,8 @@ _SIGS = [
     ("aclz_tags", _I, [_VP, _U32P, _U64]),
     ("aclz_set_range_bytes", _I, [_VP, _U32, _VP]),
     ("aclz_decode_all", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP]),
+    ("aclz_decode_all_ev", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP, _VP]),
+    ("aclz_decode_plan", _I, [_VP, ctypes.POINTER(aclz_decode_cfg), ctypes.POINTER(aclz_decode_cfg), _U32P]),
     ("aclz_device_status", _I, [_VP, _VP]),
     ("aclz_fnv", _I, [_VP, _U64, _U64P, _VP]),
     ("aclz_decode_range", _I, [_VP, _U64, _U64, _VP, _VP]),
@@ -95,6 +97,12 @@ _SIGS = [
     ("aclz_graph_create", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP, ctypes.POINTER(_VP)]),
     ("aclz_graph_launch", _I, [_VP, _VP]),
     ("aclz_graph_free", _I, [_VP]),
+    ("aclz_mlp_param_count", _U32, [_U32]),
+    ("aclz_mlp_scratch_bytes", _U64, [_U32, _U32]),
+    ("aclz_mlp_forward", _I, [_VP, _U32, _VP, _U32, _VP, _VP]),
+    ("aclz_mlp_grad", _I, [_VP, _U32, _VP, _VP, _U32, _VP, _VP, _VP, _U64, _VP]),
+    ("aclz_mlp_adam", _I, [_VP, _VP, _VP, _VP, _U32, _U32, ctypes.c_float, _VP]),
+    ("aclz_block_features", _I, [_VP, _U64, _U32, _VP, _VP]),
     ("aclz_strerror", ctypes.c_char_p, [_I]),
     ("aclz_last_cuda_error", _I, []),
 ]
@@ -260,6 +268,29 @@ def aclz_decode_all(h: int, d_out, cap: int | None = None, G: int = 32,
     _ck(lib().aclz_decode_all(h, _dptr(d_out), cap, ctypes.byref(cfg), _stream(stream)), "aclz_decode_all")
 
 
+def aclz_decode_plan(h: int, G: int = 32, mode: int = ACLZ_MODE_AUTO, ctas_per_sm: int = 0, flags: int = 0):
+    """(resolved cfg as a dict, kernel launches per aclz_decode_all call)."""
+    cfg = aclz_decode_cfg(G, mode, ctas_per_sm, flags)
+    res = aclz_decode_cfg()
+    n = ctypes.c_uint32(0)
+    _ck(lib().aclz_decode_plan(h, ctypes.byref(cfg), ctypes.byref(res), ctypes.byref(n)), "aclz_decode_plan")
+    return dict(G=res.G, mode=res.mode, ctas_per_sm=res.ctas_per_sm, flags=res.flags), int(n.value)
+
+
+def aclz_decode_all_ev(h: int, d_out, phase_event, cap: int | None = None, G: int = 32,
+                       mode: int = ACLZ_MODE_AUTO, ctas_per_sm: int = 0, flags: int = 0,
+                       stream=None) -> None:
+    """phase_event: a torch.cuda.Event (timing enabled) or a raw cudaEvent_t."""
+    if cap is None:
+        cap = int(d_out.numel() * d_out.element_size())
+    ev = phase_event if isinstance(phase_event, int) else int(phase_event.cuda_event)
+    if not ev:
+        raise ValueError("phase_event has no CUDA event yet: record it once before passing it")
+    cfg = aclz_decode_cfg(G, mode, ctas_per_sm, flags)
+    _ck(lib().aclz_decode_all_ev(h, _dptr(d_out), cap, ctypes.byref(cfg), _stream(stream), ev),
+        "aclz_decode_all_ev")
+
+
 def aclz_device_status(h: int, stream=None) -> int:
     return _ck(lib().aclz_device_status(h, _stream(stream)), "aclz_device_status")
 
@@ -325,6 +356,37 @@ def aclz_graph_launch(g: int, stream=None) -> None:
 
 def aclz_graph_free(g: int) -> None:
     _ck(lib().aclz_graph_free(g), "aclz_graph_free")
+
+
+def aclz_mlp_param_count(K: int) -> int:
+    return int(lib().aclz_mlp_param_count(K))
+
+
+def aclz_mlp_scratch_bytes(K: int, batch: int) -> int:
+    return int(lib().aclz_mlp_scratch_bytes(K, batch))
+
+
+def aclz_mlp_forward(d_params, K: int, d_x, batch: int, d_logits, stream=None) -> None:
+    _ck(lib().aclz_mlp_forward(_dptr(d_params), K, _dptr(d_x), batch, _dptr(d_logits), _stream(stream)),
+        "aclz_mlp_forward")
+
+
+def aclz_mlp_grad(d_params, K: int, d_x, d_y, batch: int, d_grad, d_loss, d_scratch, scratch_bytes=None,
+                  stream=None) -> None:
+    if scratch_bytes is None:
+        scratch_bytes = int(d_scratch.numel() * d_scratch.element_size())
+    _ck(lib().aclz_mlp_grad(_dptr(d_params), K, _dptr(d_x), _dptr(d_y), batch, _dptr(d_grad), _dptr(d_loss),
+                            _dptr(d_scratch), scratch_bytes, _stream(stream)), "aclz_mlp_grad")
+
+
+def aclz_mlp_adam(d_params, d_m, d_v, d_grad, K: int, step: int, lr: float, stream=None) -> None:
+    _ck(lib().aclz_mlp_adam(_dptr(d_params), _dptr(d_m), _dptr(d_v), _dptr(d_grad), K, step, lr, _stream(stream)),
+        "aclz_mlp_adam")
+
+
+def aclz_block_features(d_x, n: int, block_size: int, d_feat, stream=None) -> None:
+    _ck(lib().aclz_block_features(_dptr(d_x), n, block_size, _dptr(d_feat), _stream(stream)),
+        "aclz_block_features")
 
 
 def aclz_fnv(d_buf, n: int | None = None, stream=None) -> int:

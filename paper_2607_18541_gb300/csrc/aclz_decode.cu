@@ -315,12 +315,13 @@ __global__ void __launch_bounds__(kThreads) k_wave_copy(const uint4 *__restrict_
 }
 
 template <int G>
-int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st) {
+int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st, cudaEvent_t phase) {
     constexpr int gpc = kThreads / G;  // groups per CTA
     const unsigned grid0 = (h->n_blocks + gpc - 1) / gpc;
     k_wave0<G><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
                                             h->d_blk_lit, h->d_slot, (uint4 *)h->d_tri, out,
                                             h->n_blocks, h->log2_bs, nullptr, nullptr, 0);
+    if (phase) cudaEventRecord(phase, st);
     constexpr int ITEMS = 2;
     for (uint32_t w = 1; w < h->n_waves; w++) {
         const uint64_t a = h->wave_start[w], n = h->wave_start[w + 1] - a;
@@ -349,13 +350,14 @@ size_t &smem_attr() {
 // per-block done bits, then one cooperative launch runs every range of
 // waves >= 1.
 template <int G, bool STAGED>
-int launch_persistent(aclz_handle *h, uint8_t *out, uint32_t ctas_per_sm, cudaStream_t st) {
+int launch_persistent(aclz_handle *h, uint8_t *out, uint32_t ctas_per_sm, cudaStream_t st, cudaEvent_t phase) {
     constexpr int gpc = kThreads / G;
     const unsigned grid0 = (h->n_blocks + gpc - 1) / gpc;
     k_wave0<G><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
                                             h->d_blk_lit, h->d_slot, (uint4 *)h->d_tri, out,
                                             h->n_blocks, h->log2_bs, h->d_pending, h->d_done,
                                             h->n_wave_words);
+    if (phase) cudaEventRecord(phase, st);
     if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
         note_cuda_error(e);
         return ACLZ_E_CUDA;
@@ -429,22 +431,22 @@ int launch_persistent(aclz_handle *h, uint8_t *out, uint32_t ctas_per_sm, cudaSt
 }
 
 template <int G>
-int launch_persistent_auto(aclz_handle *h, uint8_t *out, const aclz_decode_cfg &c, cudaStream_t st) {
+int launch_persistent_auto(aclz_handle *h, uint8_t *out, const aclz_decode_cfg &c, cudaStream_t st,
+                           cudaEvent_t phase) {
     bool staged = h->mean_deferred_len >= (double)kTmaMin;
     if (c.flags & ACLZ_FLAG_STAGED) staged = true;
     if (c.flags & ACLZ_FLAG_REGISTERS) staged = false;
-    return staged ? launch_persistent<G, true>(h, out, c.ctas_per_sm, st)
-                  : launch_persistent<G, false>(h, out, c.ctas_per_sm, st);
+    return staged ? launch_persistent<G, true>(h, out, c.ctas_per_sm, st, phase)
+                  : launch_persistent<G, false>(h, out, c.ctas_per_sm, st, phase);
 }
 
 }  // namespace
 
-extern "C" int aclz_decode_all(aclz_handle *h, void *d_out, uint64_t cap, const aclz_decode_cfg *cfg,
-                               void *stream) {
-    if (!h || (!d_out && h->total_len)) return ACLZ_E_INVAL;
-    if (cap < h->total_len) return ACLZ_E_CAPACITY;
-    if (reinterpret_cast<uintptr_t>(d_out) & 15) return ACLZ_E_INVAL;
-    aclz_decode_cfg c = {32, ACLZ_MODE_AUTO, 0, 0};
+namespace {
+
+// Checks cfg and resolves ACLZ_MODE_AUTO for this handle.
+int resolve_cfg(const aclz_handle *h, const aclz_decode_cfg *cfg, aclz_decode_cfg &c) {
+    c = {32, ACLZ_MODE_AUTO, 0, 0};
     if (cfg) c = *cfg;
     if (c.G != 8 && c.G != 16 && c.G != 32) return ACLZ_E_INVAL;
     if (c.mode != ACLZ_MODE_WAVES && c.mode != ACLZ_MODE_PERSISTENT && c.mode != ACLZ_MODE_AUTO)
@@ -456,21 +458,60 @@ extern "C" int aclz_decode_all(aclz_handle *h, void *d_out, uint64_t cap, const 
         if (c.mode == ACLZ_MODE_PERSISTENT && !(c.flags & ACLZ_FLAG_REGISTERS)) c.flags |= ACLZ_FLAG_STAGED;
     }
     if ((c.flags & ACLZ_FLAG_STAGED) && (c.flags & ACLZ_FLAG_REGISTERS)) return ACLZ_E_INVAL;
+    if (c.mode == ACLZ_MODE_PERSISTENT && !(c.flags & (ACLZ_FLAG_STAGED | ACLZ_FLAG_REGISTERS)))
+        c.flags |= h->mean_deferred_len >= (double)kTmaMin ? ACLZ_FLAG_STAGED : ACLZ_FLAG_REGISTERS;
+    return ACLZ_OK;
+}
+
+}  // namespace
+
+extern "C" int aclz_decode_plan(const aclz_handle *h, const aclz_decode_cfg *cfg, aclz_decode_cfg *resolved,
+                                uint32_t *launches) {
+    if (!h) return ACLZ_E_INVAL;
+    aclz_decode_cfg c;
+    if (int rc = resolve_cfg(h, cfg, c)) return rc;
+    uint32_t n = 0;
+    if (h->n_blocks) {
+        n = 1;
+        if (c.mode == ACLZ_MODE_PERSISTENT) {
+            n += h->n_ranges ? 1 : 0;
+        } else {
+            for (uint32_t w = 1; w < h->n_waves; w++) n += h->wave_start[w + 1] > h->wave_start[w];
+        }
+    }
+    if (resolved) *resolved = c;
+    if (launches) *launches = n;
+    return ACLZ_OK;
+}
+
+extern "C" int aclz_decode_all_ev(aclz_handle *h, void *d_out, uint64_t cap, const aclz_decode_cfg *cfg,
+                                  void *stream, void *phase_event) {
+    if (!h || (!d_out && h->total_len)) return ACLZ_E_INVAL;
+    if (cap < h->total_len) return ACLZ_E_CAPACITY;
+    if (reinterpret_cast<uintptr_t>(d_out) & 15) return ACLZ_E_INVAL;
+    aclz_decode_cfg c;
+    if (int rc = resolve_cfg(h, cfg, c)) return rc;
     if (h->n_blocks == 0) return ACLZ_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t ev = (cudaEvent_t)phase_event;
     uint8_t *out = (uint8_t *)d_out;
     if (c.mode == ACLZ_MODE_PERSISTENT) {
         switch (c.G) {
-            case 8: return launch_persistent_auto<8>(h, out, c, st);
-            case 16: return launch_persistent_auto<16>(h, out, c, st);
-            default: return launch_persistent_auto<32>(h, out, c, st);
+            case 8: return launch_persistent_auto<8>(h, out, c, st, ev);
+            case 16: return launch_persistent_auto<16>(h, out, c, st, ev);
+            default: return launch_persistent_auto<32>(h, out, c, st, ev);
         }
     }
     switch (c.G) {
-        case 8: return launch_waves<8>(h, out, st);
-        case 16: return launch_waves<16>(h, out, st);
-        default: return launch_waves<32>(h, out, st);
+        case 8: return launch_waves<8>(h, out, st, ev);
+        case 16: return launch_waves<16>(h, out, st, ev);
+        default: return launch_waves<32>(h, out, st, ev);
     }
+}
+
+extern "C" int aclz_decode_all(aclz_handle *h, void *d_out, uint64_t cap, const aclz_decode_cfg *cfg,
+                               void *stream) {
+    return aclz_decode_all_ev(h, d_out, cap, cfg, stream, nullptr);
 }
 
 extern "C" int aclz_device_status(aclz_handle *h, void *stream) {

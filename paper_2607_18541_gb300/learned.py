@@ -1,0 +1,425 @@
+"""Learned per-block minimum-match thresholds.
+
+The paper's lever (Sec. IV-B) raises the minimum match length by distance
+class from 6/8/10/12 to 12/16/24/32 for a whole stream; its cause (Sec.
+IV-C) is that short matches to far offsets cost more offset bits than they
+save and leave the decoding warp underloaded.  Here a small network picks,
+for each 16 KiB block, one of K candidate vectors, with 12/16/24/32 as the
+fallback:
+
+* features (24 per block): 10 byte statistics computed on the GPU
+  (``aclz_block_features``), 13 statistics of a probe parse at 6/8/10/12
+  (coverage, match lengths, distance-class shares, literal runs) and the
+  block's log position;
+* labels: every candidate is encoded; a block's cost is the entropy-coded
+  size of its share of the four token streams under the stream-wide symbol
+  frequencies of that encoding; among candidates no costlier than the
+  fallback the label is the one with the fewest tokens (longest mean token,
+  the decode-speed lever of Sec. III-C);
+* training: the GPU kernels (``aclz_mlp_grad``, ``aclz_mlp_adam``);
+* inference: argmax, fallback when the top probability is below tau, then a
+  per-block check that keeps the choice only where its cost does not exceed
+  the fallback's, so the compressed size stays at or below the fixed lever's.
+
+Decoding is unchanged and bit-exact whatever the network picks.
+"""
+from __future__ import annotations
+
+import json
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+from . import aclz, synth
+
+CANDIDATES = [
+    (6, 8, 10, 12), (8, 10, 12, 16), (8, 12, 16, 24), (10, 12, 16, 24), (12, 12, 16, 24),
+    (12, 16, 20, 24), (12, 16, 24, 32), (14, 18, 24, 32), (12, 16, 24, 40), (16, 16, 24, 32),
+    (16, 24, 32, 48), (20, 24, 32, 48),
+]
+K = len(CANDIDATES)
+FALLBACK = CANDIDATES.index((12, 16, 24, 32))
+BASE = CANDIDATES.index((6, 8, 10, 12))
+BLOCK = 1 << 14
+N_FEATURES = 24
+DIST = (128, 16384, 2097152)
+
+
+# ------------------------------------------------------------ containers
+
+def read_tokens(c: np.ndarray):
+    """Token arrays of a container (format v1): per-block token counts,
+    lit_len, match_len, src, literal bytes, block size, total length."""
+    c = np.asarray(c, dtype=np.uint8)
+    hdr = c[:64]
+    total = int(hdr[8:16].view(np.uint64)[0])
+    bs = int(hdr[16:20].view(np.uint32)[0])
+    nb = int(hdr[20:24].view(np.uint32)[0])
+    nt = int(hdr[24:32].view(np.uint64)[0])
+    nl = int(hdr[32:40].view(np.uint64)[0])
+    d0, t0 = 64, 64 + 32 * nb
+    dirr = c[d0:t0].reshape(nb, 32)
+    blk = dirr[:, 16:20].copy().view(np.uint32).reshape(-1)
+    tok = c[t0:t0 + 16 * nt].copy().view(np.uint32).reshape(nt, 4)
+    ll, ml = tok[:, 0].astype(np.int64), tok[:, 1].astype(np.int64)
+    src = (tok[:, 2].astype(np.uint64) | (tok[:, 3].astype(np.uint64) << np.uint64(32))) & np.uint64((1 << 40) - 1)
+    lits = c[t0 + 16 * nt:t0 + 16 * nt + nl]
+    return blk, ll, ml, src.astype(np.int64), lits, bs, total
+
+
+def _leb128(v: np.ndarray):
+    """(bytes, owner index) of the LEB128 encodings of v, value after value."""
+    v = np.asarray(v, dtype=np.int64)
+    nbytes = np.ones(v.size, dtype=np.int64)
+    for k in range(1, 10):
+        nbytes += (v >> (7 * k)) > 0
+    start = np.concatenate([[0], np.cumsum(nbytes)])[:-1]
+    out = np.zeros(int(nbytes.sum()), dtype=np.int64)
+    for k in range(int(nbytes.max()) if v.size else 0):
+        sel = nbytes > k
+        more = (nbytes[sel] > k + 1).astype(np.int64)
+        out[start[sel] + k] = ((v[sel] >> (7 * k)) & 0x7F) | (more << 7)
+    return out, np.repeat(np.arange(v.size), nbytes)
+
+
+def _streams(c):
+    """The four byte streams of the entropy estimate with, for each byte, the
+    block it belongs to: literals, LEB128 lit_len, LEB128 match_len, source
+    positions as w little-endian bytes (w = fewest bytes holding total-1)."""
+    blk, ll, ml, src, lits, bs, total = read_tokens(c)
+    tb = np.repeat(np.arange(blk.size), blk)
+    lb = np.repeat(tb, ll) if lits.size else np.zeros(0, dtype=np.int64)
+    lb_bytes, lb_i = _leb128(ll)
+    mb_bytes, mb_i = _leb128(ml)
+    w = 1
+    while w < 8 and total > 1 and ((total - 1) >> (8 * w)) != 0:
+        w += 1
+    m = ml > 0
+    ob = np.stack([(src[m] >> (8 * k)) & 0xFF for k in range(w)], axis=1).reshape(-1)
+    obi = np.repeat(tb[m], w)
+    return [(lits.astype(np.int64), lb), (lb_bytes, tb[lb_i]), (mb_bytes, tb[mb_i]), (ob, obi)], blk.size
+
+
+def est_bytes(c) -> float:
+    """Estimated entropy-coded size of a container: header + directory +
+    order-0 cost of 64 KiB tiles of the four token streams + 512 bytes of
+    table per tile (an ideal tile coder standing in for tile-ANS, Sec. II)."""
+    streams, nb = _streams(c)
+    tot = 64.0 + 32.0 * nb
+    for s, _ in streams:
+        for off in range(0, s.size, 65536):
+            t = s[off:off + 65536]
+            cnt = np.bincount(t, minlength=256).astype(np.float64)
+            p = cnt[cnt > 0] / t.size
+            tot += float(-(cnt[cnt > 0] * np.log2(p)).sum()) / 8.0 + 512.0
+    return tot
+
+
+def block_costs(c) -> np.ndarray:
+    """Per-block cost in bytes: each byte of the four streams priced at
+    -log2 of its stream-wide frequency, summed by owning block."""
+    streams, nb = _streams(c)
+    cost = np.zeros(nb)
+    for s, owner in streams:
+        if not s.size:
+            continue
+        cnt = np.bincount(s, minlength=256).astype(np.float64)
+        price = np.zeros(256)
+        nz = cnt > 0
+        price[nz] = -np.log2(cnt[nz] / s.size) / 8.0
+        cost += np.bincount(owner, weights=price[s], minlength=nb)
+    return cost
+
+
+def parse_features(c) -> np.ndarray:
+    """13 statistics of a parse per block: coverage, mean match length / 64,
+    matches < 16 and < 32, shares per distance class, mean literal run / 16,
+    matches per KiB / 64, mean log2 distance / 24, matches >= 64, tokens per
+    KiB / 64."""
+    blk, ll, ml, src, lits, bs, total = read_tokens(c)
+    nb = blk.size
+    tb = np.repeat(np.arange(nb), blk)
+    pos = np.concatenate([[0], np.cumsum(ll + ml)])[:-1] + ll   # match position of each token
+    m = ml > 0
+    d = np.where(m, pos - src, 1)
+    cls = np.searchsorted(np.array(DIST), d, side="right")
+    blen = np.minimum(bs, total - np.arange(nb) * bs).astype(np.float64)
+    def bsum(w):
+        return np.bincount(tb, weights=w, minlength=nb)
+    nm = bsum(m.astype(np.float64))
+    nmz = np.maximum(nm, 1.0)
+    f = np.zeros((nb, 13))
+    f[:, 0] = bsum(np.where(m, ml, 0)) / blen
+    f[:, 1] = bsum(np.where(m, ml, 0)) / nmz / 64.0
+    f[:, 2] = bsum((m & (ml < 16)).astype(np.float64)) / nmz
+    f[:, 3] = bsum((m & (ml < 32)).astype(np.float64)) / nmz
+    for k in range(4):
+        f[:, 4 + k] = bsum((m & (cls == k)).astype(np.float64)) / nmz
+    f[:, 8] = bsum(ll.astype(np.float64)) / np.maximum(bsum(np.ones(tb.size)), 1.0) / 16.0
+    f[:, 9] = nm / (blen / 1024.0) / 64.0
+    f[:, 10] = bsum(np.where(m, np.log2(np.maximum(d, 1)), 0.0)) / nmz / 24.0
+    f[:, 11] = bsum((m & (ml >= 64)).astype(np.float64)) / nmz
+    f[:, 12] = blk / (blen / 1024.0) / 64.0
+    return f
+
+
+def encode(x, mm=None, block_mm=None, block_size: int = BLOCK, chain_depth: int = 16, threads: int = 0):
+    """Host encode at one threshold vector, or per-block vectors (block_mm:
+    [n_blocks, 4] uint8)."""
+    p = aclz.aclz_encode_params_default(0)
+    p.block_size = block_size
+    p.chain_depth = chain_depth
+    if mm is not None:
+        for i in range(4):
+            p.min_match[i] = mm[i]
+    return aclz.aclz_encode(x, p, block_min_match=block_mm, threads=threads)
+
+
+def features(x, base_container, block_size: int = BLOCK, stream=None) -> np.ndarray:
+    """[n_blocks, 24] features: GPU byte statistics, probe-parse statistics,
+    log2 of (1 + block index) / 24."""
+    import torch
+    n = int(x.size)
+    nb = (n + block_size - 1) // block_size
+    dx = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    df = torch.empty(nb * 10, dtype=torch.float32, device="cuda")
+    aclz.aclz_block_features(dx, n, block_size, df, stream=stream)
+    raw = df.view(nb, 10).cpu().numpy().astype(np.float64)
+    pf = parse_features(base_container)
+    posf = (np.log2(1.0 + np.arange(nb)) / 24.0)[:, None]
+    return np.concatenate([raw, pf, posf], axis=1)
+
+
+def label_data(x, block_size: int = BLOCK, threads: int = 0):
+    """Features and labels of one training stream; also the per-candidate
+    block costs and token counts."""
+    threads = threads or min(K, os.cpu_count() or 1)
+    per = max(1, (os.cpu_count() or 1) // threads)
+    with ThreadPoolExecutor(threads) as ex:
+        cs = list(ex.map(lambda mm: encode(x, mm, block_size=block_size, threads=per), CANDIDATES))
+    costs = np.stack([block_costs(c) for c in cs])          # [K, nb]
+    ntok = np.stack([read_tokens(c)[0].astype(np.float64) for c in cs])
+    ok = costs <= costs[FALLBACK][None, :] + 1e-9
+    key = np.where(ok, ntok + costs / (1.0 + costs.max()), np.inf)
+    y = np.argmin(key, axis=0).astype(np.int32)
+    return features(x, cs[BASE], block_size), y, costs, ntok
+
+
+class Model:
+    """Parameters on the GPU, trained with the library's kernels."""
+
+    def __init__(self, seed: int = 20260712):
+        import torch
+        self.torch = torch
+        self.P = aclz.aclz_mlp_param_count(K)
+        rng = np.random.default_rng(seed)
+        parts = []
+        for fan_in, fan_out in ((N_FEATURES, 64), (64, 64), (64, K)):
+            parts.append(rng.standard_normal(fan_in * fan_out) * np.sqrt(2.0 / fan_in))
+            parts.append(np.zeros(fan_out))
+        self.params = torch.from_numpy(np.concatenate(parts).astype(np.float32)).cuda()
+        self.mean = np.zeros(N_FEATURES)
+        self.std = np.ones(N_FEATURES)
+
+    def standardize(self, f):
+        return ((f - self.mean) / self.std).astype(np.float32)
+
+    def fit(self, f, y, steps: int = 2000, batch: int = 256, lr: float = 1e-3, seed: int = 1, log_every: int = 0):
+        torch = self.torch
+        self.mean = f.mean(axis=0)
+        self.std = f.std(axis=0) + 1e-6
+        X = torch.from_numpy(self.standardize(f)).cuda()
+        Y = torch.from_numpy(np.asarray(y, dtype=np.int32)).cuda()
+        assert int(Y.min()) >= 0 and int(Y.max()) < K
+        m = torch.zeros_like(self.params)
+        v = torch.zeros_like(self.params)
+        g = torch.empty_like(self.params)
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        scratch = torch.empty(aclz.aclz_mlp_scratch_bytes(K, batch), dtype=torch.uint8, device="cuda")
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(seed)
+        xb = torch.empty(batch, N_FEATURES, dtype=torch.float32, device="cuda")
+        yb = torch.empty(batch, dtype=torch.int32, device="cuda")
+        hist = []
+        n = X.shape[0]
+        for step in range(1, steps + 1):
+            idx = torch.randint(0, n, (batch,), device="cuda", generator=gen)
+            torch.index_select(X, 0, idx, out=xb)
+            torch.index_select(Y, 0, idx, out=yb)
+            aclz.aclz_mlp_grad(self.params, K, xb, yb, batch, g, loss, scratch)
+            aclz.aclz_mlp_adam(self.params, m, v, g, K, step, lr)
+            if log_every and step % log_every == 0:
+                hist.append((step, float(loss.item())))
+        return hist
+
+    def logits(self, f):
+        torch = self.torch
+        X = torch.from_numpy(self.standardize(f)).cuda()
+        out = torch.empty(X.shape[0], K, dtype=torch.float32, device="cuda")
+        aclz.aclz_mlp_forward(self.params, K, X, X.shape[0], out)
+        return out.cpu().numpy()
+
+    def choose(self, f, tau: float = 0.0):
+        z = self.logits(f)
+        z = z - z.max(axis=1, keepdims=True)
+        p = np.exp(z) / np.exp(z).sum(axis=1, keepdims=True)
+        k = p.argmax(axis=1)
+        k[p.max(axis=1) < tau] = FALLBACK
+        return k
+
+    def save(self, path: str):
+        with open(path, "w") as fh:
+            json.dump(dict(K=K, candidates=CANDIDATES, mean=self.mean.tolist(), std=self.std.tolist(),
+                           params=self.params.cpu().numpy().tolist()), fh)
+
+    @classmethod
+    def load(cls, path: str):
+        import torch
+        with open(path) as fh:
+            d = json.load(fh)
+        m = cls()
+        m.params = torch.tensor(d["params"], dtype=torch.float32, device="cuda")
+        m.mean, m.std = np.array(d["mean"]), np.array(d["std"])
+        return m
+
+
+def encode_learned(model: Model, x, block_size: int = BLOCK, tau: float = 0.0, passes: int = 3):
+    """Per-block thresholds from the network, judged against the fixed
+    12/16/24/32 encode: a block keeps the network's pick only where it has no
+    more tokens (the decode-speed lever) and no higher cost than under the
+    fallback.  A block's parse depends only on its own thresholds, so token
+    counts are exact; costs use stream-wide frequencies, so the check is
+    repeated, and if the whole-stream estimate still exceeds the fallback's
+    the fallback container is returned.  Returns (container, choices)."""
+    base = encode(x, CANDIDATES[BASE], block_size=block_size)
+    fb = encode(x, CANDIDATES[FALLBACK], block_size=block_size)
+    fb_cost = block_costs(fb)
+    fb_tok = read_tokens(fb)[0]
+    fb_est = est_bytes(fb)
+    k = model.choose(features(x, base, block_size), tau)
+    for i in range(passes + 1):
+        if np.all(k == FALLBACK):
+            return fb, k
+        bmm = np.array([CANDIDATES[j] for j in k], dtype=np.uint8)
+        c = encode(x, block_mm=bmm, block_size=block_size)
+        worse = (k != FALLBACK) & ((block_costs(c) > fb_cost + 1e-9) | (read_tokens(c)[0] > fb_tok))
+        if not worse.any():
+            if est_bytes(c) <= fb_est:
+                return c, k
+            break
+        if i == passes:
+            break
+        k[worse] = FALLBACK
+    k[:] = FALLBACK
+    return fb, k
+
+
+def training_streams(scale: int = 1):
+    """Training data (seeds disjoint from evaluation): FASTQ-like, Markov
+    bytes and word text."""
+    out = []
+    for i in range(2):
+        out.append(synth.fastq((32 << 20) * scale, seed=0x7A0000 + i))
+        out.append(synth.markov2((8 << 20) * scale, seed=0x7B0000 + i))
+        out.append(synth.wordtext((8 << 20) * scale, seed=0x7C0000 + i, chunk_bytes=1 << 22))
+    return out
+
+
+# ------------------------------------------------------------ gain benchmark
+
+def _decode_gbs(c, n: int, reps: int = 5, **cfg):
+    """(median output GB/s of decode_all, output equals the input) for one container."""
+    import torch
+    from .autotune import measure
+    st = torch.cuda.current_stream()
+    h = aclz.aclz_upload(c, st)
+    try:
+        out = torch.empty(max(16, (n + 15) // 16 * 16), dtype=torch.uint8, device="cuda")
+        ms = measure(h, out, reps=reps, stream=st, **cfg)
+        return n / ms / 1e6, out[:n]
+    finally:
+        aclz.aclz_free(h)
+
+
+def train_default(scale: int = 1, steps: int = 2000, seed: int = 20260712, log=print):
+    feats, labels = [], []
+    for s in training_streams(scale):
+        f, y, _, _ = label_data(s)
+        feats.append(f)
+        labels.append(y)
+    f = np.concatenate(feats)
+    y = np.concatenate(labels)
+    log(json.dumps({"train_blocks": int(y.size), "label_hist": np.bincount(y, minlength=K).tolist()}))
+    model = Model(seed)
+    hist = model.fit(f, y, steps=steps, batch=256, lr=1e-3, log_every=max(1, steps // 4))
+    acc = float((model.choose(f) == y).mean())
+    log(json.dumps({"train_loss": [round(v, 4) for _, v in hist], "train_acc": round(acc, 3)}))
+    return model
+
+
+def gain_single(model: Model, x, block_size: int = BLOCK, reps: int = 5):
+    """One stream at 6/8/10/12, 12/16/24/32 and learned per-block thresholds:
+    estimated ratio, tokens and decode GB/s (AUTO mode), output checked."""
+    import torch
+    rows = []
+    xd = torch.from_numpy(x).cuda()
+    for name, c in (("6/8/10/12", encode(x, CANDIDATES[BASE], block_size=block_size)),
+                    ("12/16/24/32", encode(x, CANDIDATES[FALLBACK], block_size=block_size)),
+                    ("learned", encode_learned(model, x, block_size)[0])):
+        gbs, out = _decode_gbs(c, x.size, reps)
+        rows.append(dict(thresholds=name, bytes=int(x.size), est_ratio=round(x.size / est_bytes(c), 4),
+                         tokens=int(read_tokens(c)[0].sum()), decode_gbs=round(gbs, 1),
+                         exact=bool(torch.equal(out, xd))))
+    return rows
+
+
+def gain_batched(model: Model, n: int = 512, lo: int = 16 << 10, hi: int = 4 << 20, reps: int = 5):
+    """Fixed 12/16/24/32 streams decoded one at a time (single-stream decode)
+    against learned per-block thresholds with one batched, graph-captured
+    decode; ratio = total bytes / total estimated bytes."""
+    import torch
+    from . import batched
+    streams = batched.make_streams(n, lo, hi)
+    total = int(sum(s.size for s in streams))
+    fixed = [encode(s, CANDIDATES[FALLBACK], threads=1) for s in streams]
+    learned_c = [encode_learned(model, s)[0] for s in streams]
+    ms_one, outs = batched.time_one_by_one(fixed, reps=reps)
+    ok_one = all(torch.equal(o[:s.size].cpu(), torch.from_numpy(s)) for o, s in zip(outs, streams))
+    dec = batched.BatchDecoder(learned_c)
+    try:
+        ms_b = batched.time_batched(dec, reps=reps)
+        ok_b = all(torch.equal(dec.stream_output(i).cpu(), torch.from_numpy(s)) for i, s in enumerate(streams))
+    finally:
+        dec.close()
+    return [dict(form="fixed 12/16/24/32, one stream at a time", streams=n, bytes=total,
+                 est_ratio=round(total / sum(est_bytes(c) for c in fixed), 4),
+                 decode_gbs=round(total / ms_one / 1e6, 2), exact=ok_one),
+            dict(form="learned per-block, batched graph decode", streams=n, bytes=total,
+                 est_ratio=round(total / sum(est_bytes(c) for c in learned_c), 4),
+                 decode_gbs=round(total / ms_b / 1e6, 2), exact=ok_b)]
+
+
+def main():
+    import argparse
+    ap = argparse.ArgumentParser(description="train the threshold network and measure its gain")
+    ap.add_argument("--fastq-mib", type=int, default=256)
+    ap.add_argument("--markov-mib", type=int, default=128)
+    ap.add_argument("--streams", type=int, default=512)
+    ap.add_argument("--train-scale", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--save", default="")
+    a = ap.parse_args()
+    model = train_default(a.train_scale, a.steps)
+    if a.save:
+        model.save(a.save)
+    for name, x in (("fastq", synth.fastq(a.fastq_mib << 20, seed=0x7A1000)),
+                    ("markov", synth.markov2(a.markov_mib << 20, seed=0x7B1000))):
+        for r in gain_single(model, x):
+            print(json.dumps(dict(workload=name, **r)), flush=True)
+    for r in gain_batched(model, a.streams):
+        print(json.dumps(dict(workload="batched", **r)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -28,7 +28,7 @@ PERSIST_REGS = (aclz.ACLZ_MODE_PERSISTENT, aclz.ACLZ_FLAG_REGISTERS)
 MODES = (WAVES, PERSIST_STAGED, PERSIST_REGS)
 
 
-def gpu_decode(c, G=32, mode=WAVES, fnv=True, range_bytes=None):
+def gpu_decode(c, G=32, mode=WAVES, fnv=True, range_bytes=None, ctas_per_sm=0, phase_event=None):
     s = torch.cuda.current_stream()
     h = aclz.aclz_upload(c, s)
     try:
@@ -36,7 +36,11 @@ def gpu_decode(c, G=32, mode=WAVES, fnv=True, range_bytes=None):
         if range_bytes:
             aclz.aclz_set_range_bytes(h, range_bytes, s)
         out = torch.empty(max(16, (info.total_len + 15) // 16 * 16), dtype=torch.uint8, device="cuda")
-        aclz.aclz_decode_all(h, out, G=G, mode=mode[0], flags=mode[1], stream=s)
+        if phase_event is not None:
+            aclz.aclz_decode_all_ev(h, out, phase_event, G=G, mode=mode[0], flags=mode[1],
+                                    ctas_per_sm=ctas_per_sm, stream=s)
+        else:
+            aclz.aclz_decode_all(h, out, G=G, mode=mode[0], flags=mode[1], ctas_per_sm=ctas_per_sm, stream=s)
         assert aclz.aclz_device_status(h, s) == aclz.ACLZ_OK
         got = out[:info.total_len].cpu().numpy()
         f = aclz.aclz_fnv(out, info.total_len, stream=s) if fnv else None
@@ -255,6 +259,42 @@ def test_output_buffer_checks():
         aclz.aclz_free(h)
 
 
+# ------------------------------------------------- phase event and plan
+
+@pytest.mark.parametrize("L", [32, 1024])
+def test_phase_event_and_plan(L):
+    sw = synth.copy_sweep(24 << 20, 1 << 15, L, seed=synth.SEED_COPY + 7 * L)
+    c = aclz.aclz_pack(sw.total, sw.block_size, (4, 4, 4, 4), sw.blk_ntok, sw.lit_len, sw.match_len,
+                       sw.src, sw.literals)
+    exp = oracle.decode(oracle.pack_sweep(sw, tags=False))
+    s = torch.cuda.current_stream()
+    h = aclz.aclz_upload(c, s)
+    try:
+        counts = aclz.aclz_wave_counts(h)
+        plan, n = aclz.aclz_decode_plan(h, mode=aclz.ACLZ_MODE_WAVES)
+        assert plan["mode"] == aclz.ACLZ_MODE_WAVES and n == 1 + int((counts[1:] > 0).sum())
+        plan, n = aclz.aclz_decode_plan(h, mode=aclz.ACLZ_MODE_PERSISTENT)
+        assert plan["mode"] == aclz.ACLZ_MODE_PERSISTENT and n == 2
+        assert plan["flags"] in (aclz.ACLZ_FLAG_STAGED, aclz.ACLZ_FLAG_REGISTERS)
+        plan, n = aclz.aclz_decode_plan(h)
+        # AUTO: persistent with staging for long deferred matches, waves for short ones
+        assert plan["mode"] == (aclz.ACLZ_MODE_PERSISTENT if L == 1024 else aclz.ACLZ_MODE_WAVES)
+        with pytest.raises(aclz.AclzError):
+            aclz.aclz_decode_plan(h, G=12)
+        out = torch.empty(sw.total, dtype=torch.uint8, device="cuda")
+        a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        m.record(s)
+        out.zero_()
+        a.record(s)
+        aclz.aclz_decode_all_ev(h, out, m, stream=s)
+        b.record(s)
+        b.synchronize()
+        assert a.elapsed_time(m) > 0 and m.elapsed_time(b) > 0
+        assert np.array_equal(out.cpu().numpy(), exp)
+    finally:
+        aclz.aclz_free(h)
+
+
 # ------------------------------------------------------------------- FNV
 
 @pytest.mark.parametrize("n", [0, 1, 65535, 65536, 65537, (3 << 20) + 5])
@@ -279,3 +319,9 @@ def test_copy_sweep_1gib_full_size(L):
         got, f, info = gpu_decode(c, 32, mode)
         assert np.array_equal(got, exp)
         assert f == fe
+    # the benchmark's exact launch: AUTO, 2 CTAs per SM, 8 KiB ranges, phase event
+    ev = torch.cuda.Event(enable_timing=True)
+    ev.record()
+    got, f, info = gpu_decode(c, 32, (aclz.ACLZ_MODE_AUTO, 0), range_bytes=8192, ctas_per_sm=2, phase_event=ev)
+    assert np.array_equal(got, exp)
+    assert f == fe

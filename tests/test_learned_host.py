@@ -1,0 +1,111 @@
+"""Host-side parts of the learned per-block thresholds (no GPU): the size
+estimate agrees with the oracle's, per-block costs add up to the whole
+stream's order-0 cost, parse statistics agree with the oracle's token
+statistics, and the candidate set holds the fallback and the base vector."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_18541_gb300 import aclz, learned, synth
+from paper_2607_18541_gb300 import build as libbuild
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    libbuild.build()
+    aclz.lib()
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    # FASTQ-like records then Markov bytes: blocks that want different lengths
+    return np.concatenate([synth.fastq(300_000, seed=11), synth.markov2(200_000, seed=12)])
+
+
+def test_candidates_hold_the_paper_vectors():
+    assert learned.CANDIDATES[learned.FALLBACK] == (12, 16, 24, 32)
+    assert learned.CANDIDATES[learned.BASE] == (6, 8, 10, 12)
+    assert 2 <= learned.K <= 16
+    assert len(set(learned.CANDIDATES)) == learned.K
+    for mm in learned.CANDIDATES:
+        assert list(mm) == sorted(mm) and mm[0] >= 4
+
+
+@pytest.mark.parametrize("mm", [(6, 8, 10, 12), (12, 16, 24, 32)])
+def test_est_bytes_equals_oracle(mixed, mm):
+    c = learned.encode(mixed, mm, block_size=1 << 14)
+    assert learned.est_bytes(c) == pytest.approx(oracle.est_bytes(c), rel=1e-12)
+
+
+def test_block_costs_sum_to_stream_order0_cost(mixed):
+    c = learned.encode(mixed, (6, 8, 10, 12), block_size=1 << 14)
+    costs = learned.block_costs(c)
+    streams, nb = learned._streams(c)
+    assert costs.shape == (nb,)
+    want = 0.0
+    for s, _ in streams:
+        cnt = np.bincount(s, minlength=256).astype(np.float64)
+        p = cnt[cnt > 0] / s.size
+        want += float(-(cnt[cnt > 0] * np.log2(p)).sum()) / 8
+    assert costs.sum() == pytest.approx(want, rel=1e-10)
+    assert np.all(costs > 0)
+
+
+def test_parse_features_agree_with_oracle_stats(mixed):
+    bs = 1 << 14
+    c = learned.encode(mixed, (6, 8, 10, 12), block_size=bs)
+    f = learned.parse_features(c)
+    blk, ll, ml, src, lits, _, total = learned.read_tokens(c)
+    nb = blk.size
+    assert f.shape == (nb, 13)
+    # per block: rebuild a one-block container's statistics with the oracle
+    for b in (0, nb // 2, nb - 1):
+        t0 = int(blk[:b].sum())
+        t1 = t0 + int(blk[b])
+        pos = int(min(b * bs, total))
+        nm = 0
+        mbytes = 0
+        lt16 = lt32 = 0
+        cls = [0, 0, 0, 0]
+        for i in range(t0, t1):
+            pos += int(ll[i])
+            if ml[i]:
+                nm += 1
+                mbytes += int(ml[i])
+                lt16 += ml[i] < 16
+                lt32 += ml[i] < 32
+                cls[oracle.dist_class(pos - int(src[i]))] += 1
+                pos += int(ml[i])
+        blen = min(bs, total - b * bs)
+        assert f[b, 0] == pytest.approx(mbytes / blen)
+        if nm:
+            assert f[b, 2] == pytest.approx(lt16 / nm)
+            assert f[b, 3] == pytest.approx(lt32 / nm)
+            assert np.allclose(f[b, 4:8], np.array(cls) / nm)
+        assert f[b, 12] == pytest.approx(int(blk[b]) / (blen / 1024) / 64)
+    # whole-stream totals equal the oracle's statistics
+    st = oracle.stats(c)
+    blen = np.minimum(bs, total - np.arange(nb) * bs)
+    assert round(float((f[:, 0] * blen).sum())) == st.match_bytes
+
+
+def test_read_tokens_matches_oracle_reader(mixed):
+    c = learned.encode(mixed, (12, 16, 24, 32), block_size=1 << 15)
+    blk, ll, ml, src, lits, bs, total = learned.read_tokens(c)
+    oblk, oll, oml, osrc, _, olits = oracle.tokens(c)
+    assert np.array_equal(blk, oblk) and np.array_equal(ll, oll) and np.array_equal(ml, oml)
+    assert np.array_equal(src.astype(np.uint64), osrc)
+    assert np.array_equal(lits, olits[:lits.size]) and lits.size == oracle.header(c).n_literals
+    assert bs == 1 << 15 and total == mixed.size
+
+
+def test_per_block_thresholds_encode_like_the_oracle(mixed):
+    bs = 1 << 14
+    nb = -(-mixed.size // bs)
+    k = np.arange(nb) % learned.K
+    bmm = np.array([learned.CANDIDATES[i] for i in k], dtype=np.uint8)
+    got = learned.encode(mixed, block_mm=bmm, block_size=bs)
+    # the host encoder leaves wave tags to the GPU upload
+    want = oracle.strip_tags(oracle.encode(mixed, bs, block_mm=bmm, chain_depth=16))
+    assert np.array_equal(got, want)
+    assert np.array_equal(oracle.decode(got), mixed)
