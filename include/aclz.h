@@ -172,7 +172,7 @@ int aclz_decode_all(aclz_handle *h, void *d_out, uint64_t cap, const aclz_decode
 
 /* aclz_decode_all that also records phase_event (a cudaEvent_t owned by the
  * caller) on stream between its two phases: after the wave-0 kernel
- * (literals and in-order matches, Sec. III-B) and before the deferred
+ * (literals and in-order matches; the wavefront decode of Sec. I) and before the deferred
  * matches of waves >= 1.  With its own events before and after the call a
  * caller times each phase on the launching stream.  phase_event NULL is
  * aclz_decode_all; a failed record is reported by the next CUDA call. */

@@ -284,16 +284,21 @@ class Model:
         return m
 
 
-def encode_learned(model: Model, x, block_size: int = BLOCK, tau: float = 0.0, passes: int = 3):
+def encode_learned(model: Model, x, block_size: int = BLOCK, tau: float = 0.0, passes: int = 3,
+                   base=None, fb=None):
     """Per-block thresholds from the network, judged against the fixed
     12/16/24/32 encode: a block keeps the network's pick only where it has no
     more tokens (the decode-speed lever) and no higher cost than under the
     fallback.  A block's parse depends only on its own thresholds, so token
     counts are exact; costs use stream-wide frequencies, so the check is
     repeated, and if the whole-stream estimate still exceeds the fallback's
-    the fallback container is returned.  Returns (container, choices)."""
-    base = encode(x, CANDIDATES[BASE], block_size=block_size)
-    fb = encode(x, CANDIDATES[FALLBACK], block_size=block_size)
+    the fallback container is returned.  base / fb: the containers at
+    6/8/10/12 and 12/16/24/32 if already encoded.  Returns (container,
+    choices)."""
+    if base is None:
+        base = encode(x, CANDIDATES[BASE], block_size=block_size)
+    if fb is None:
+        fb = encode(x, CANDIDATES[FALLBACK], block_size=block_size)
     fb_cost = block_costs(fb)
     fb_tok = read_tokens(fb)[0]
     fb_est = est_bytes(fb)
@@ -364,13 +369,15 @@ def gain_single(model: Model, x, block_size: int = BLOCK, reps: int = 5):
     import torch
     rows = []
     xd = torch.from_numpy(x).cuda()
-    for name, c in (("6/8/10/12", encode(x, CANDIDATES[BASE], block_size=block_size)),
-                    ("12/16/24/32", encode(x, CANDIDATES[FALLBACK], block_size=block_size)),
-                    ("learned", encode_learned(model, x, block_size)[0])):
+    base = encode(x, CANDIDATES[BASE], block_size=block_size)
+    fb = encode(x, CANDIDATES[FALLBACK], block_size=block_size)
+    lc, k = encode_learned(model, x, block_size, base=base, fb=fb)
+    for name, c in (("6/8/10/12", base), ("12/16/24/32", fb), ("learned", lc)):
         gbs, out = _decode_gbs(c, x.size, reps)
         rows.append(dict(thresholds=name, bytes=int(x.size), est_ratio=round(x.size / est_bytes(c), 4),
                          tokens=int(read_tokens(c)[0].sum()), decode_gbs=round(gbs, 1),
                          exact=bool(torch.equal(out, xd))))
+    rows[-1]["choices"] = np.bincount(k, minlength=K).tolist()
     return rows
 
 
@@ -383,7 +390,7 @@ def gain_batched(model: Model, n: int = 512, lo: int = 16 << 10, hi: int = 4 << 
     streams = batched.make_streams(n, lo, hi)
     total = int(sum(s.size for s in streams))
     fixed = [encode(s, CANDIDATES[FALLBACK], threads=1) for s in streams]
-    learned_c = [encode_learned(model, s)[0] for s in streams]
+    learned_c = [encode_learned(model, s, fb=f)[0] for s, f in zip(streams, fixed)]
     ms_one, outs = batched.time_one_by_one(fixed, reps=reps)
     ok_one = all(torch.equal(o[:s.size].cpu(), torch.from_numpy(s)) for o, s in zip(outs, streams))
     dec = batched.BatchDecoder(learned_c)
