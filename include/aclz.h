@@ -143,6 +143,22 @@ int aclz_wave_counts(const aclz_handle *h, uint64_t *counts, uint32_t cap);
  * to host memory. */
 int aclz_tags(const aclz_handle *h, uint32_t *host_tags, uint64_t cap);
 
+/* Re-point every deferred match at the bytes it copies that are final
+ * after wave 0 (literal bytes or in-order match bytes), splitting it into
+ * pieces, and rebuild the decode schedule as two waves: wave 0, then all
+ * pieces, which are independent.  Absolute back-references (abstract;
+ * Sec. I) make this exact: a match may copy equal bytes from wherever the
+ * match that wrote them read them.  Removes the chains that force many
+ * waves in the wavefront decode (Sec. I) on data whose copies copy copies
+ * (for example FASTQ-like records at 6/8/10/12).  Decode output is
+ * unchanged; afterwards aclz_handle_info reports n_waves = 2 and
+ * n_deferred = the number of pieces (16 B of device memory each), and
+ * aclz_tags still returns the container's wave tags.  Pointer doubling on
+ * the GPU, about log2(waves) + 1 rounds.  Synchronizes the stream; no
+ * decode of h may be in flight.  Idempotent.  ACLZ_E_NOMEM when the pieces
+ * do not fit, ACLZ_E_UNSUPPORTED beyond 2^32 - 16 pieces. */
+int aclz_flatten(aclz_handle *h, void *stream);
+
 /* Regroup the persistent schedule: consecutive (block, wave) segments are
  * packed into work ranges of about range_bytes of deferred matches (upload
  * picks 16 KiB).  Synchronizes the stream.  Used by the autotuner. */

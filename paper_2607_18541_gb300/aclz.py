@@ -84,6 +84,7 @@ _SIGS = [
     ("aclz_wave_counts", _I, [_VP, _U64P, _U32]),
     ("aclz_tags", _I, [_VP, _U32P, _U64]),
     ("aclz_set_range_bytes", _I, [_VP, _U32, _VP]),
+    ("aclz_flatten", _I, [_VP, _VP]),
     ("aclz_decode_all", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP]),
     ("aclz_decode_all_ev", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP, _VP]),
     ("aclz_decode_plan", _I, [_VP, ctypes.POINTER(aclz_decode_cfg), ctypes.POINTER(aclz_decode_cfg), _U32P]),
@@ -253,6 +254,10 @@ def aclz_tags(h: int) -> np.ndarray:
     out = np.zeros(max(1, nt), dtype=np.uint32)
     _ck(lib().aclz_tags(h, out.ctypes.data_as(_U32P), nt), "aclz_tags")
     return out[:nt]
+
+
+def aclz_flatten(h: int, stream=None) -> None:
+    _ck(lib().aclz_flatten(h, _stream(stream)), "aclz_flatten")
 
 
 def aclz_set_range_bytes(h: int, range_bytes: int, stream=None) -> None:

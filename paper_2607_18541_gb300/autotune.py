@@ -53,7 +53,8 @@ def measure(h: int, out, reps: int = 5, warmup: int = 2, stream=None, **cfg) -> 
 def tune(build, total: int, block_sizes=(8192, 16384, 32768, 65536, 131072), Gs=(8, 16, 32),
          ctas=(0, 2), range_bytes=(8192, 16384), top: int = 4, reps: int = 5, stream=None) -> dict:
     """build(block_size) -> container bytes of the same data at that block
-    size.  Returns {"best": {...}, "trials": [...]} with output GB/s."""
+    size; total = the data's bytes (GB/s are total / time).  Returns
+    {"best": {...}, "trials": [...]}."""
     import torch
     cands = []
     for bs in block_sizes:
@@ -67,13 +68,17 @@ def tune(build, total: int, block_sizes=(8192, 16384, 32768, 65536, 131072), Gs=
     # the `top` best-predicted block sizes, each with its best-predicted G
     chosen = sorted(((max(v)[0], bs, max(v)[1]) for bs, v in keep.items()), reverse=True)[:top]
     trials = []
-    out = torch.empty(max(16, (total + 15) // 16 * 16), dtype=torch.uint8, device="cuda")
+    out = None
     st = stream or torch.cuda.current_stream()
     for pred, bs, G in chosen:
         c = build(bs)
         h = aclz.aclz_upload(c, st)
         try:
             info = aclz.aclz_handle_info(h)
+            # a merged batch is longer than its streams (block-aligned bases)
+            need = max(16, (int(info.total_len) + 15) // 16 * 16)
+            if out is None or out.numel() < need:
+                out = torch.empty(need, dtype=torch.uint8, device="cuda")
             for G2 in sorted({G, 32}):
                 for cps in ctas:
                     for rb in range_bytes:

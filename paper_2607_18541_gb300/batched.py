@@ -135,3 +135,76 @@ def time_one_by_one(containers, stream=None, reps: int = 3, **cfg):
     finally:
         for h in hs:
             aclz.aclz_free(h)
+
+
+def main():
+    """Full-size batched benchmark: 4096 streams, output sizes log-uniform
+    16 KiB - 64 MiB (half Markov bytes, half FASTQ-like), encoded at
+    12/16/24/32; block size, G, CTAs per SM and range size tuned on a sample
+    of the streams; then one graph-captured batched decode of all streams
+    against the same containers decoded one at a time.  Prints JSON lines."""
+    import argparse
+    import json
+    import torch
+    from . import autotune
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--streams", type=int, default=4096)
+    ap.add_argument("--lo", type=int, default=16 << 10)
+    ap.add_argument("--hi", type=int, default=64 << 20)
+    ap.add_argument("--chain-depth", type=int, default=1)
+    ap.add_argument("--tune-sample", type=int, default=256)
+    ap.add_argument("--reps", type=int, default=5)
+    a = ap.parse_args()
+    t0 = time.time()
+    streams = make_streams(a.streams, a.lo, a.hi)
+    total = int(sum(x.size for x in streams))
+    t_gen = time.time() - t0
+
+    def params(bs):
+        p = aclz.aclz_encode_params_default(aclz.ACLZ_PRESET_TUNED)
+        p.block_size = bs
+        p.chain_depth = a.chain_depth
+        return p
+
+    step = max(1, a.streams // a.tune_sample)
+    sample = streams[::step]
+    t0 = time.time()
+    tuned = autotune.tune(lambda bs: aclz.aclz_batch_merge(encode_streams(sample, params(bs)))[0],
+                          int(sum(x.size for x in sample)), block_sizes=(16384, 32768, 65536, 131072),
+                          top=3, reps=3)
+    best = tuned["best"]
+    t_tune = time.time() - t0
+    print(json.dumps({"tuned_on_streams": len(sample), "best": best, "tune_s": round(t_tune, 1)}), flush=True)
+    t0 = time.time()
+    cs = encode_streams(streams, params(best["block_size"]))
+    t_enc = time.time() - t0
+    cfg = dict(G=best["G"], ctas_per_sm=best["ctas_per_sm"])
+    st = torch.cuda.current_stream()
+    dec = BatchDecoder(cs, stream=st)
+    try:
+        aclz.aclz_set_range_bytes(dec.h, best["range_bytes"], st)
+        info = aclz.aclz_handle_info(dec.h)
+        ms_b = time_batched(dec, reps=a.reps, graph=True, **cfg)
+        if aclz.aclz_device_status(dec.h, st) != aclz.ACLZ_OK:
+            raise RuntimeError("batched decode reported a device error")
+        exact = 0
+        for i, x in enumerate(streams):
+            exact += bool(torch.equal(dec.stream_output(i), torch.from_numpy(x).to("cuda", non_blocking=True)))
+        row_b = dict(form="batched: one persistent graph-captured launch", streams=len(streams), bytes=total,
+                     blocks=info.n_blocks, waves=info.n_waves, lanes=best["G"] * info.n_blocks,
+                     ms=round(ms_b, 3), gbs=round(total / ms_b / 1e6, 1), exact_streams=exact, **cfg,
+                     block_size=best["block_size"], range_bytes=best["range_bytes"])
+    finally:
+        dec.close()
+    print(json.dumps(row_b), flush=True)
+    ms_1, outs = time_one_by_one(cs, stream=st, reps=1, **cfg)
+    exact1 = sum(bool(torch.equal(o[:x.size], torch.from_numpy(x).to("cuda"))) for o, x in zip(outs, streams))
+    del outs
+    print(json.dumps(dict(form="one stream at a time (single-stream decode)", streams=len(streams), bytes=total,
+                          ms=round(ms_1, 3), gbs=round(total / ms_1 / 1e6, 2), exact_streams=exact1,
+                          gen_s=round(t_gen, 1), encode_s=round(t_enc, 1), chain_depth=a.chain_depth)),
+          flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -50,21 +50,23 @@ __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long l
     return v;
 }
 
-constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits: about a second at most
-
-// A bounded wait gives up when the limit runs out or when another group
-// already gave up (err has kErrTimeout), so one stuck wait ends the whole
-// launch within about a second.
+// Bounded waits: spin_limit polls (sleeping up to 256 ns each) before a wait
+// gives up.  The host scales it with the wave count, from 2^22 (about a
+// second) to 2^26: a range deep in a long chain legitimately waits for most
+// of the launch.  A wait also gives up when another group already gave up
+// (err has kErrTimeout), so one stuck wait ends the whole launch.
+constexpr uint32_t kSpinLimitMin = 1u << 22, kSpinLimitMax = 1u << 26;
 
 // Spin (bounded) until every wave below w of one block is done: its done
 // bits (ww 64-bit words, empty waves preset) are all set below bit w.
-__device__ __forceinline__ bool wait_waves_below(const unsigned long long *done, uint32_t w, uint32_t *err) {
+__device__ __forceinline__ bool wait_waves_below(const unsigned long long *done, uint32_t w, uint32_t *err,
+                                                 uint32_t spin_limit) {
     for (uint32_t k = 0; k * 64 < w; k++) {
         const uint32_t nbits = w - k * 64;
         const unsigned long long want = nbits >= 64 ? ~0ULL : ((1ULL << nbits) - 1ULL);
         uint32_t spins = 0;
         while ((ld_acquire64(done + k) & want) != want) {
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 atomicOr(err, kErrTimeout);
                 return false;
             }
@@ -104,7 +106,7 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
         const uint64_t dl = pos + incl - (ll + ml);
         const uint64_t dm = dl + ll;
         // deferred matches go to their wave's worklist
-        if (v && ml && tag) {
+        if (tri && v && ml && tag) {
             const uint32_t sl = __ldg(slot + i);
             __stcg(tri + sl, make_uint4((uint32_t)dm, (uint32_t)(dm >> 32), (uint32_t)src,
                                         (uint32_t)(src >> 32) | (ml << 8)));
@@ -170,7 +172,7 @@ template <int G, bool STAGED>
 __global__ void __launch_bounds__(kThreads, STAGED ? 1 : 3)
     k_ranges(const uint4 *__restrict__ ranges, uint64_t n_ranges, const uint4 *__restrict__ seg,
              unsigned long long *done, uint32_t ww, const uint4 *__restrict__ tri, uint8_t *out,
-             uint32_t log2bs, uint32_t stage_bytes, uint32_t *err) {
+             uint32_t log2bs, uint32_t stage_bytes, uint32_t *err, uint32_t spin_limit) {
     extern __shared__ __align__(128) uint8_t smem[];
     Group<G> g;
     constexpr int kGroups = kThreads / G;
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, STAGED ? 1 : 3)
             if (v) {
                 const uint64_t b0 = sr >> log2bs, b1 = (sr + len - 1) >> log2bs;
                 for (uint64_t bb = b0; bb <= b1; bb++)
-                    if (!wait_waves_below(done + bb * ww, w, err)) ok = false;
+                    if (!wait_waves_below(done + bb * ww, w, err, spin_limit)) ok = false;
             }
             g.sync();
             // segment starts inside this window (block changes)
@@ -319,7 +321,7 @@ int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st, cudaEvent_t phas
     constexpr int gpc = kThreads / G;  // groups per CTA
     const unsigned grid0 = (h->n_blocks + gpc - 1) / gpc;
     k_wave0<G><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
-                                            h->d_blk_lit, h->d_slot, (uint4 *)h->d_tri, out,
+                                            h->d_blk_lit, h->d_slot, h->flat ? nullptr : (uint4 *)h->d_tri, out,
                                             h->n_blocks, h->log2_bs, nullptr, nullptr, 0);
     if (phase) cudaEventRecord(phase, st);
     constexpr int ITEMS = 2;
@@ -354,7 +356,7 @@ int launch_persistent(aclz_handle *h, uint8_t *out, uint32_t ctas_per_sm, cudaSt
     constexpr int gpc = kThreads / G;
     const unsigned grid0 = (h->n_blocks + gpc - 1) / gpc;
     k_wave0<G><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
-                                            h->d_blk_lit, h->d_slot, (uint4 *)h->d_tri, out,
+                                            h->d_blk_lit, h->d_slot, h->flat ? nullptr : (uint4 *)h->d_tri, out,
                                             h->n_blocks, h->log2_bs, h->d_pending, h->d_done,
                                             h->n_wave_words);
     if (phase) cudaEventRecord(phase, st);
@@ -414,7 +416,9 @@ int launch_persistent(aclz_handle *h, uint8_t *out, uint32_t ctas_per_sm, cudaSt
     uint32_t log2bs = h->log2_bs;
     uint32_t sb = o.stage_bytes;
     uint32_t *err = h->d_err;
-    void *args[] = {&ranges, &n_ranges, &seg, &done, &ww, &tri, &out, &log2bs, &sb, &err};
+    uint32_t spin_limit =
+        (uint32_t)std::min<uint64_t>(kSpinLimitMax, (uint64_t)kSpinLimitMin * std::max<uint32_t>(1u, h->n_waves / 256));
+    void *args[] = {&ranges, &n_ranges, &seg, &done, &ww, &tri, &out, &log2bs, &sb, &err, &spin_limit};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kThreads), args, o.smem, st);
     if (e == cudaErrorCooperativeLaunchTooLarge && o.per_sm > 1) {
         // fewer co-resident CTAs than the occupancy estimate: one per SM

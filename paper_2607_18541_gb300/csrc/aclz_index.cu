@@ -474,7 +474,8 @@ int cuda_rc(cudaError_t e) {
 
 // Exclusive scan of n u32 in place (device), total to *d_total (device).
 // Temporary partials are allocated stream-ordered.
-static int device_excl_scan(uint32_t *d, uint64_t n, uint32_t *d_total, cudaStream_t st) {
+int aclz::device_excl_scan(uint32_t *d, uint64_t n, uint32_t *d_total, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
     const uint64_t ntile = (n + kScanTile - 1) / kScanTile;
     uint32_t *part = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&part, sizeof(uint32_t) * (ntile + 1), st);

@@ -55,6 +55,10 @@ int parse_container(const uint8_t *c, uint64_t n, View *v, bool check_directory)
 // Remember the last CUDA runtime error for aclz_last_cuda_error().
 void note_cuda_error(int cuda_error_code);
 
+// Exclusive scan of n u32 in place on the device, the total to *d_total
+// (device); stream-ordered, temporary storage allocated on the stream.
+int device_excl_scan(uint32_t *d, uint64_t n, uint32_t *d_total, void *stream);
+
 // Matches per work range for a target byte size of deferred matches.
 inline uint32_t range_matches(uint32_t range_bytes, double mean_len) {
     double t = mean_len > 0 ? (double)range_bytes / mean_len : 16.0;
@@ -100,4 +104,8 @@ struct aclz_handle {
     uint32_t n_wave_words = 0;
     uint64_t *d_pending = nullptr;
     uint64_t *d_done = nullptr;
+    // set by aclz_flatten: the deferred work items are origin pieces in one
+    // wave, built at flatten time (wave 0 writes no triplets)
+    bool flat = false;
+    uint64_t n_matches_deferred = 0;  // deferred matches before flattening
 };

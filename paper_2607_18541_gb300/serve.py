@@ -175,10 +175,11 @@ def main():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--loads", default="0.25,0.5,0.75,0.9")
     ap.add_argument("--max-size", type=int, default=256 << 20)
+    ap.add_argument("--chain-depth", type=int, default=4)
     a = ap.parse_args()
     total = int(a.corpus_gib * (1 << 30))
     t0 = time.time()
-    x, c = build_corpus(total)
+    x, c = build_corpus(total, chain_depth=a.chain_depth)
     t_build = time.time() - t0
     h = aclz.aclz_upload(c, torch.cuda.current_stream())
     try:
@@ -186,8 +187,8 @@ def main():
         rows = serve_benchmark(h, total, a.requests, tuple(float(v) for v in a.loads.split(",")),
                                hi=a.max_size)
         for r in rows:
-            r.update(corpus_bytes=total, compressed_bytes=int(c.size), block_size=info.block_size,
-                     build_s=round(t_build, 1))
+            r.update(corpus_bytes=total, container_bytes=int(c.size), block_size=info.block_size,
+                     waves=info.n_waves, chain_depth=a.chain_depth, build_s=round(t_build, 1))
             print(json.dumps(r), flush=True)
     finally:
         aclz.aclz_free(h)

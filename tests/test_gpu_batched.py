@@ -65,3 +65,32 @@ def test_merged_oracle_tags_are_kept_and_decoded():
             assert np.array_equal(got[int(o):int(o) + x.size], x)
     finally:
         aclz.aclz_free(h)
+
+
+def test_autotune_on_a_merged_batch_and_decode_with_its_choice():
+    from paper_2607_18541_gb300 import autotune
+    streams = batched.make_streams(24, 16 << 10, 512 << 10, seed=77)
+    total = int(sum(x.size for x in streams))
+
+    def build(bs):
+        p = aclz.aclz_encode_params_default(aclz.ACLZ_PRESET_TUNED)
+        p.block_size = bs
+        return aclz.aclz_batch_merge(batched.encode_streams(streams, p))[0]
+
+    res = autotune.tune(build, total, block_sizes=(4096, 16384), Gs=(16, 32), ctas=(0, 2),
+                        range_bytes=(8192,), top=2, reps=2)
+    best = res["best"]
+    assert best["gbs"] > 0 and len(res["trials"]) >= 2
+    p = aclz.aclz_encode_params_default(aclz.ACLZ_PRESET_TUNED)
+    p.block_size = best["block_size"]
+    s = torch.cuda.current_stream()
+    dec = batched.BatchDecoder(batched.encode_streams(streams, p), stream=s)
+    try:
+        aclz.aclz_set_range_bytes(dec.h, best["range_bytes"], s)
+        dec.capture(G=best["G"], ctas_per_sm=best["ctas_per_sm"])
+        dec.replay()
+        assert aclz.aclz_device_status(dec.h, s) == 0
+        for i, x in enumerate(streams):
+            assert np.array_equal(dec.stream_output(i).cpu().numpy(), x), i
+    finally:
+        dec.close()

@@ -28,10 +28,13 @@ PERSIST_REGS = (aclz.ACLZ_MODE_PERSISTENT, aclz.ACLZ_FLAG_REGISTERS)
 MODES = (WAVES, PERSIST_STAGED, PERSIST_REGS)
 
 
-def gpu_decode(c, G=32, mode=WAVES, fnv=True, range_bytes=None, ctas_per_sm=0, phase_event=None):
+def gpu_decode(c, G=32, mode=WAVES, fnv=True, range_bytes=None, ctas_per_sm=0, phase_event=None,
+               flatten=False):
     s = torch.cuda.current_stream()
     h = aclz.aclz_upload(c, s)
     try:
+        if flatten:
+            aclz.aclz_flatten(h, s)
         info = aclz.aclz_handle_info(h)
         if range_bytes:
             aclz.aclz_set_range_bytes(h, range_bytes, s)
@@ -255,6 +258,50 @@ def test_output_buffer_checks():
         assert e.value.code == aclz.ACLZ_E_INVAL
         with pytest.raises(aclz.AclzError):
             aclz.aclz_decode_all(h, buf, G=12, stream=s)
+    finally:
+        aclz.aclz_free(h)
+
+
+# ------------------------------------------------------------ flatten
+
+def _flatten_case(kind):
+    if kind == "fastq_base":
+        return oracle.encode(synth.fastq(1 << 20, seed=41), 1 << 12, oracle.PRESET_BASE, chain_depth=16)
+    if kind == "markov_base":
+        return oracle.encode(synth.markov2(1 << 20, seed=42), 1 << 13, oracle.PRESET_BASE, chain_depth=16)
+    if kind == "text_tuned":
+        return oracle.encode(synth.wordtext(1 << 20, seed=43, chunk_bytes=1 << 20), 1 << 14, oracle.PRESET_TUNED,
+                             chain_depth=16)
+    if kind == "tiny_blocks":
+        return oracle.encode(synth.fastq(200_000, seed=44), 64, oracle.PRESET_BASE, chain_depth=8)
+    L = int(kind[5:])
+    sw = synth.copy_sweep(6 << 20, 1 << 15, L, seed=synth.SEED_COPY + 3 * L)
+    return oracle.pack_sweep(sw)
+
+
+@pytest.mark.parametrize("kind", ["fastq_base", "markov_base", "text_tuned", "tiny_blocks", "sweep1024",
+                                  "sweep32"])
+def test_flatten_decodes_identically(kind):
+    c = _flatten_case(kind)
+    exp = oracle.decode(c)
+    fe = oracle.fnv_chunked(exp)
+    before = oracle.header(c).n_waves
+    for mode in MODES:
+        got, f, info = gpu_decode(c, 32, mode, flatten=True)
+        assert np.array_equal(got, exp), mode
+        assert f == fe
+        assert info["n_waves"] == (2 if before > 1 else before)
+    # flatten is idempotent and keeps the container's tags
+    s = torch.cuda.current_stream()
+    h = aclz.aclz_upload(c, s)
+    try:
+        tags = aclz.aclz_tags(h)
+        aclz.aclz_flatten(h, s)
+        aclz.aclz_flatten(h, s)
+        assert np.array_equal(aclz.aclz_tags(h), tags)
+        out = torch.empty(len(exp) + 16, dtype=torch.uint8, device="cuda")
+        aclz.aclz_decode_all(h, out, G=16, stream=s)
+        assert np.array_equal(out[:len(exp)].cpu().numpy(), exp)
     finally:
         aclz.aclz_free(h)
 
