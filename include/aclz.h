@@ -130,6 +130,17 @@ typedef struct aclz_handle aclz_handle;
  * stream.  ACLZ_E_CORRUPT for an invalid container. */
 int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_handle **out);
 
+/* aclz_upload with options.  ACLZ_UPLOAD_FLATTEN: build the two-wave
+ * flattened schedule of aclz_flatten directly.  For a container without
+ * tags, the upload then needs only whether each match is in order within
+ * its block (wave 0) or not, which every block settles on its own: no
+ * ordered pass over the blocks, so deep chains of copies do not slow the
+ * upload, and aclz_tags returns these 0/1 tags.  A container with tags has
+ * them checked as by aclz_upload first.  flags other than
+ * ACLZ_UPLOAD_FLATTEN: ACLZ_E_INVAL. */
+#define ACLZ_UPLOAD_FLATTEN 1u
+int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out);
+
 /* Free a handle and its device memory (after its work has completed). */
 int aclz_free(aclz_handle *h);
 

@@ -29,6 +29,7 @@ ACLZ_E_TIMEOUT = -6
 ACLZ_E_DEVICE = -7
 ACLZ_E_UNSUPPORTED = -8
 ACLZ_PRESET_BASE, ACLZ_PRESET_TUNED, ACLZ_PRESET_PUSH = 0, 1, 2
+ACLZ_UPLOAD_FLATTEN = 1
 ACLZ_MODE_WAVES, ACLZ_MODE_PERSISTENT, ACLZ_MODE_AUTO = 0, 1, 2
 ACLZ_FLAG_STAGED, ACLZ_FLAG_REGISTERS = 1, 2
 
@@ -79,6 +80,7 @@ _SIGS = [
     ("aclz_pack_bytes", _U64, [_U64, _U32, _U64, _U64]),
     ("aclz_container_info", _I, [_VP, _U64, ctypes.POINTER(aclz_info)]),
     ("aclz_upload", _I, [_VP, _U64, _VP, ctypes.POINTER(_VP)]),
+    ("aclz_upload_ex", _I, [_VP, _U64, _U32, _VP, ctypes.POINTER(_VP)]),
     ("aclz_free", _I, [_VP]),
     ("aclz_handle_info", _I, [_VP, ctypes.POINTER(aclz_info)]),
     ("aclz_wave_counts", _I, [_VP, _U64P, _U32]),
@@ -224,11 +226,14 @@ def aclz_container_info(buf) -> aclz_info:
 
 # ------------------------------------------------------------------ device
 
-def aclz_upload(buf, stream=None) -> int:
-    """Returns the handle as an integer."""
+def aclz_upload(buf, stream=None, flags: int = 0) -> int:
+    """Returns the handle as an integer; flags = ACLZ_UPLOAD_* (aclz_upload_ex)."""
     c = _np_u8(buf)
     h = ctypes.c_void_p(0)
-    _ck(lib().aclz_upload(_hptr(c), c.size, _stream(stream), ctypes.byref(h)), "aclz_upload")
+    if flags:
+        _ck(lib().aclz_upload_ex(_hptr(c), c.size, flags, _stream(stream), ctypes.byref(h)), "aclz_upload_ex")
+    else:
+        _ck(lib().aclz_upload(_hptr(c), c.size, _stream(stream), ctypes.byref(h)), "aclz_upload")
     return int(h.value)
 
 

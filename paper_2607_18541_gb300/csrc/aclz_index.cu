@@ -126,6 +126,79 @@ __device__ uint32_t match_requirement(const uint4 *__restrict__ tok, const uint6
     return req;
 }
 
+// Requirement of match i when only wave 0 versus later matters (the
+// flattened schedule): 0 when every source byte lies in block b and is a
+// literal byte or a byte of an in-order (tag 0) match of the block, else 1.
+// Sets *inwin when a covering token has index >= win0.
+__device__ uint32_t local_requirement(const uint4 *__restrict__ tok, const uint64_t *__restrict__ blk_tok,
+                                      const uint32_t *__restrict__ tokdst, const uint32_t *tags, uint64_t src,
+                                      uint64_t ml, uint32_t b, uint32_t log2bs, uint64_t win0, bool *inwin) {
+    const uint64_t bstart = (uint64_t)b << log2bs;
+    if ((src >> log2bs) != b || ((src + ml - 1) >> log2bs) != b) return 1;
+    uint64_t lo = blk_tok[b], hi = blk_tok[b + 1] - 1;
+    const uint32_t rel = (uint32_t)(src - bstart);
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(tokdst + mid) <= rel) lo = mid; else hi = mid - 1;
+    }
+    const uint64_t e = src + ml;
+    uint32_t req = 0;
+    for (uint64_t t = lo; t < blk_tok[b + 1]; t++) {
+        const uint64_t ts = bstart + __ldg(tokdst + t);
+        if (ts >= e) break;
+        const uint4 tk = __ldg(tok + t);
+        const uint64_t le = ts + tk.x;
+        if (tk.y && le < e && le + tk.y > src) {
+            req = max(req, min(__ldcg(tags + t), 1u));
+            if (t >= win0) *inwin = true;
+        }
+    }
+    return req;
+}
+
+// Wave-0-or-later tags for the flattened schedule: one warp per block, no
+// cross-block waits (a source in another block is always "later"); in-window
+// dependencies resolved by iterating the window to its fixed point.
+__global__ void __launch_bounds__(256) k_tags_local(const uint4 *__restrict__ tok,
+                                                    const uint64_t *__restrict__ blk_tok,
+                                                    const uint32_t *__restrict__ tokdst, uint32_t *tags,
+                                                    uint32_t nb, uint32_t log2bs, uint32_t *maxtag) {
+    Group<32> g;
+    const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nb) return;
+    const uint64_t t0 = blk_tok[b], t1 = blk_tok[b + 1];
+    uint32_t mx = 0;
+    for (uint64_t w = t0; w < t1; w += 32) {
+        const uint64_t i = w + g.lane;
+        const bool v = i < t1;
+        const uint4 t = v ? __ldg(tok + i) : make_uint4(0, 0, 0, 0);
+        const uint64_t ml = t.y;
+        const uint64_t src = ((uint64_t)t.z | ((uint64_t)t.w << 32)) & kSrcMask;
+        const bool m = v && ml;
+        if (v) __stcg(tags + i, 0u);
+        __threadfence_block();
+        g.sync();
+        bool pending = m;
+        uint32_t cur = 0;
+        for (int it = 0; it < 40; it++) {
+            bool inwin = false, changed = false;
+            if (pending) {
+                const uint32_t req = local_requirement(tok, blk_tok, tokdst, tags, src, ml, b, log2bs, w, &inwin);
+                changed = req != cur;
+                cur = req;
+            }
+            if (changed) __stcg(tags + i, cur);
+            __threadfence_block();
+            g.sync();
+            pending = pending && inwin;
+            if (!g.ballot(changed) || !g.ballot(pending)) break;
+        }
+        if (m) mx = max(mx, cur);
+    }
+    for (int o = 16; o; o >>= 1) mx = max(mx, g.shfl(mx, (g.lane + o) & 31));
+    if (g.lane == 0) atomicMax(maxtag, mx);
+}
+
 // Minimal tags.  Warps take blocks in increasing order from a counter; a
 // block's matches whose sources lie in earlier blocks wait (bounded) for
 // those blocks' done flags; in-window dependencies are resolved by
@@ -489,6 +562,12 @@ int aclz::device_excl_scan(uint32_t *d, uint64_t n, uint32_t *d_total, void *str
 }
 
 extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_handle **out) {
+    return aclz_upload_ex(host_buf, n, 0, stream, out);
+}
+
+extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out) {
+    if (flags & ~(uint32_t)ACLZ_UPLOAD_FLATTEN) return ACLZ_E_INVAL;
+    const bool flat_up = (flags & ACLZ_UPLOAD_FLATTEN) != 0;
     if (!host_buf || !out) return ACLZ_E_INVAL;
     *out = nullptr;
     View v;
@@ -567,6 +646,10 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
         k_extract_tags<<<1024, 256, 0, st>>>((const uint4 *)h->d_tok, d_tags, nt);
         k_tags_check<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_tokdst,
                                                d_tags, nb, h->log2_bs, nt, d_maxtag, h->d_err);
+    } else if (flat_up) {
+        k_tags_local<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_tokdst, d_tags, nb,
+                                               h->log2_bs, d_maxtag);
+        k_store_tags<<<1024, 256, 0, st>>>((uint4 *)h->d_tok, d_tags, nt);
     } else {
         CK(cudaMalloc(&done.p, 4 * nb));
         CK(cudaMemsetAsync(done.p, 0, 4 * nb, st));
@@ -656,6 +739,10 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
     }
     CK(cudaMalloc((void **)&h->d_done, 8 * (size_t)nb * h->n_wave_words));
     CK(cudaStreamSynchronize(st));
+    if (flat_up) {
+        rc = aclz_flatten(h, stream);
+        if (rc) { cleanup(); return rc; }
+    }
     *out = h;
     return ACLZ_OK;
 }

@@ -306,6 +306,40 @@ def test_flatten_decodes_identically(kind):
         aclz.aclz_free(h)
 
 
+@pytest.mark.parametrize("kind", ["fastq_base", "text_tuned", "tiny_blocks", "sweep1024", "sweep32"])
+def test_flatten_upload_without_tags(kind):
+    """Upload with ACLZ_UPLOAD_FLATTEN of an untagged container: the 0/1
+    tags are exactly 'minimal tag > 0', and every mode decodes the bytes."""
+    c = oracle.strip_tags(_flatten_case(kind))
+    exp = oracle.decode(c)
+    mt, _ = oracle.min_tags(c)
+    s = torch.cuda.current_stream()
+    h = aclz.aclz_upload(c, s, flags=aclz.ACLZ_UPLOAD_FLATTEN)
+    try:
+        assert np.array_equal(aclz.aclz_tags(h), (mt > 0).astype(np.uint32))
+        info = aclz.aclz_handle_info(h)
+        assert info.n_waves <= 2
+        out = torch.empty(len(exp) + 16, dtype=torch.uint8, device="cuda")
+        for mode, flags in MODES:
+            out.zero_()
+            aclz.aclz_decode_all(h, out, mode=mode, flags=flags, stream=s)
+            assert aclz.aclz_device_status(h, s) == 0
+            assert np.array_equal(out[:len(exp)].cpu().numpy(), exp), (mode, flags)
+        # seek is unaffected
+        lo, hi = len(exp) // 3, len(exp) // 3 + 100_000
+        part = torch.empty(hi - lo + 16, dtype=torch.uint8, device="cuda")
+        aclz.aclz_decode_range(h, lo, hi, part, stream=s)
+        assert np.array_equal(part[:hi - lo].cpu().numpy(), exp[lo:hi])
+    finally:
+        aclz.aclz_free(h)
+
+
+def test_upload_ex_rejects_unknown_flags():
+    c = _flatten_case("markov_base")
+    with pytest.raises(aclz.AclzError):
+        aclz.aclz_upload(c, torch.cuda.current_stream(), flags=6)
+
+
 # ------------------------------------------------- phase event and plan
 
 @pytest.mark.parametrize("L", [32, 1024])
