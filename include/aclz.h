@@ -170,6 +170,18 @@ int aclz_tags(const aclz_handle *h, uint32_t *host_tags, uint64_t cap);
  * do not fit, ACLZ_E_UNSUPPORTED beyond 2^32 - 16 pieces. */
 int aclz_flatten(aclz_handle *h, void *stream);
 
+/* Shorten the copy chains of the wavefront schedule: `rounds` rounds of the
+ * pointer doubling of aclz_flatten (each halving the chains a match's
+ * source bytes go through), after which every deferred match is rewritten
+ * as consecutive tokens, one per piece (the first keeps its literal run),
+ * and the decode index (minimal wave tags, worklists, schedule) is rebuilt
+ * for them.  Fewer waves (about halved per round) for more, shorter
+ * matches.  Decode and seek output are unchanged; aclz_handle_info then
+ * reports the new token and wave counts and aclz_tags the new tags.
+ * rounds 0 (or no deferred match) is a no-op; rounds > 32 or a flattened
+ * handle: ACLZ_E_INVAL.  Synchronizes; no decode of h may be in flight. */
+int aclz_reshape(aclz_handle *h, uint32_t rounds, void *stream);
+
 /* Regroup the persistent schedule: consecutive (block, wave) segments are
  * packed into work ranges of about range_bytes of deferred matches (upload
  * picks 16 KiB).  Synchronizes the stream.  Used by the autotuner. */

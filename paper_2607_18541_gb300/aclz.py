@@ -87,6 +87,7 @@ _SIGS = [
     ("aclz_tags", _I, [_VP, _U32P, _U64]),
     ("aclz_set_range_bytes", _I, [_VP, _U32, _VP]),
     ("aclz_flatten", _I, [_VP, _VP]),
+    ("aclz_reshape", _I, [_VP, _U32, _VP]),
     ("aclz_decode_all", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP]),
     ("aclz_decode_all_ev", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP, _VP]),
     ("aclz_decode_plan", _I, [_VP, ctypes.POINTER(aclz_decode_cfg), ctypes.POINTER(aclz_decode_cfg), _U32P]),
@@ -263,6 +264,10 @@ def aclz_tags(h: int) -> np.ndarray:
 
 def aclz_flatten(h: int, stream=None) -> None:
     _ck(lib().aclz_flatten(h, _stream(stream)), "aclz_flatten")
+
+
+def aclz_reshape(h: int, rounds: int, stream=None) -> None:
+    _ck(lib().aclz_reshape(h, rounds, _stream(stream)), "aclz_reshape")
 
 
 def aclz_set_range_bytes(h: int, range_bytes: int, stream=None) -> None:

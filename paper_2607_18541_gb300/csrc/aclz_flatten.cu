@@ -224,46 +224,47 @@ int rc_of(cudaError_t e) {
 
 unsigned grid_for(uint64_t n) { return (unsigned)std::min<uint64_t>((n + 255) / 256, 152ull * 32); }
 
-}  // namespace
+// Pieces of every deferred match after up to max_rounds doubling rounds
+// (fewer when no piece overlaps deferred bytes any more: final).
+struct Pieces {
+    Dev defscan, P, owner, off, dmk;
+    uint64_t np = 0, D = 0;
+    unsigned long long def_bytes = 0;
+    bool final = false;
+};
 
-extern "C" int aclz_flatten(aclz_handle *h, void *stream) {
-    if (!h) return ACLZ_E_INVAL;
-    if (h->flat) return ACLZ_OK;
-    cudaStream_t st = (cudaStream_t)stream;
+int make_pieces(aclz_handle *h, cudaStream_t st, int max_rounds, Pieces &pc) {
     const uint64_t nt = h->n_tokens, D = h->n_deferred;
     const uint32_t nb = h->n_blocks;
-    if (D == 0) {
-        h->flat = true;
-        return ACLZ_OK;
-    }
+    pc.D = D;
     // deferred matches in token order: defscan[t] = rank, defscan[nt] = D
-    Dev defscan, work;
-    FCK(cudaMalloc(&defscan.p, 4 * (nt + 1)));
+    Dev work;
+    FCK(cudaMalloc(&pc.defscan.p, 4 * (nt + 1)));
     FCK(cudaMalloc(&work.p, 64));
     uint32_t *d_any = work.as<uint32_t>(), *d_total = work.as<uint32_t>() + 1;
     unsigned long long *d_bytes = (unsigned long long *)(work.as<char>() + 8);
     FCK(cudaMemsetAsync(work.p, 0, 64, st));
-    k_is_deferred<<<grid_for(nt), 256, 0, st>>>((const uint4 *)h->d_tok, nt, defscan.as<uint32_t>());
+    k_is_deferred<<<grid_for(nt), 256, 0, st>>>((const uint4 *)h->d_tok, nt, pc.defscan.as<uint32_t>());
     FCK(cudaGetLastError());
-    if (int rc = device_excl_scan(defscan.as<uint32_t>(), nt, defscan.as<uint32_t>() + nt, st)) return rc;
-    // round 0
-    Dev P, owner, off, dmk;
+    if (int rc = device_excl_scan(pc.defscan.as<uint32_t>(), nt, pc.defscan.as<uint32_t>() + nt, st)) return rc;
+    // round 0: one piece per match
     uint64_t np = D;
-    FCK(cudaMalloc(&P.p, 16 * np));
-    FCK(cudaMalloc(&owner.p, 4 * np));
-    FCK(cudaMalloc(&off.p, 8 * (D + 1)));
-    FCK(cudaMalloc(&dmk.p, 8 * D));
-    FCK(cudaMemcpyAsync(off.as<uint64_t>() + D, &np, 8, cudaMemcpyHostToDevice, st));
+    FCK(cudaMalloc(&pc.P.p, 16 * np));
+    FCK(cudaMalloc(&pc.owner.p, 4 * np));
+    FCK(cudaMalloc(&pc.off.p, 8 * (D + 1)));
+    FCK(cudaMalloc(&pc.dmk.p, 8 * D));
+    FCK(cudaMemcpyAsync(pc.off.as<uint64_t>() + D, &np, 8, cudaMemcpyHostToDevice, st));
     k_fl_init<<<(nb + 7) / 8, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_tokdst,
-                                             defscan.as<uint32_t>(), nb, h->log2_bs, P.as<uint4>(),
-                                             owner.as<uint32_t>(), off.as<uint64_t>(), dmk.as<uint64_t>(), d_bytes);
+                                             pc.defscan.as<uint32_t>(), nb, h->log2_bs, pc.P.as<uint4>(),
+                                             pc.owner.as<uint32_t>(), pc.off.as<uint64_t>(), pc.dmk.as<uint64_t>(),
+                                             d_bytes);
     FCK(cudaGetLastError());
-    unsigned long long def_bytes = 0;
-    FCK(cudaMemcpyAsync(&def_bytes, d_bytes, 8, cudaMemcpyDeviceToHost, st));
+    FCK(cudaMemcpyAsync(&pc.def_bytes, d_bytes, 8, cudaMemcpyDeviceToHost, st));
+    pc.final = false;
     for (int round = 0;; round++) {
         if (round > 64) return ACLZ_E_UNSUPPORTED;
-        FlatIdx ix{(const uint4 *)h->d_tok, h->d_blk_tok, h->d_tokdst, defscan.as<uint32_t>(), P.as<uint4>(),
-                   off.as<uint64_t>(), h->log2_bs};
+        FlatIdx ix{(const uint4 *)h->d_tok, h->d_blk_tok, h->d_tokdst, pc.defscan.as<uint32_t>(), pc.P.as<uint4>(),
+                   pc.off.as<uint64_t>(), h->log2_bs};
         Dev cnt;
         FCK(cudaMalloc(&cnt.p, 4 * np + 4));
         FCK(cudaMemsetAsync(d_any, 0, 4, st));
@@ -272,7 +273,11 @@ extern "C" int aclz_flatten(aclz_handle *h, void *stream) {
         uint32_t any = 0;
         FCK(cudaMemcpyAsync(&any, d_any, 4, cudaMemcpyDeviceToHost, st));
         FCK(cudaStreamSynchronize(st));
-        if (!any) break;
+        if (!any) {
+            pc.final = true;
+            break;
+        }
+        if (round >= max_rounds) break;
         if (int rc = device_excl_scan(cnt.as<uint32_t>(), np, d_total, st)) return rc;
         uint32_t total = 0;
         FCK(cudaMemcpyAsync(&total, d_total, 4, cudaMemcpyDeviceToHost, st));
@@ -282,17 +287,38 @@ extern "C" int aclz_flatten(aclz_handle *h, void *stream) {
         FCK(cudaMalloc(&P2.p, 16 * (uint64_t)total));
         FCK(cudaMalloc(&owner2.p, 4 * (uint64_t)total));
         FCK(cudaMalloc(&off2.p, 8 * (D + 1)));
-        k_fl_emit<<<grid_for(np), 256, 0, st>>>(ix, np, cnt.as<uint32_t>(), owner.as<uint32_t>(), P2.as<uint4>(),
-                                                 owner2.as<uint32_t>());
-        k_fl_off<<<grid_for(D + 1), 256, 0, st>>>(off.as<uint64_t>(), D, np, cnt.as<uint32_t>(), d_total,
+        k_fl_emit<<<grid_for(np), 256, 0, st>>>(ix, np, cnt.as<uint32_t>(), pc.owner.as<uint32_t>(),
+                                                 P2.as<uint4>(), owner2.as<uint32_t>());
+        k_fl_off<<<grid_for(D + 1), 256, 0, st>>>(pc.off.as<uint64_t>(), D, np, cnt.as<uint32_t>(), d_total,
                                                    off2.as<uint64_t>());
         FCK(cudaGetLastError());
         FCK(cudaStreamSynchronize(st));
-        std::swap(P.p, P2.p);
-        std::swap(owner.p, owner2.p);
-        std::swap(off.p, off2.p);
+        std::swap(pc.P.p, P2.p);
+        std::swap(pc.owner.p, owner2.p);
+        std::swap(pc.off.p, off2.p);
         np = total;
     }
+    pc.np = np;
+    return ACLZ_OK;
+}
+
+}  // namespace
+
+extern "C" int aclz_flatten(aclz_handle *h, void *stream) {
+    if (!h) return ACLZ_E_INVAL;
+    if (h->flat) return ACLZ_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t D = h->n_deferred;
+    const uint32_t nb = h->n_blocks;
+    if (D == 0) {
+        h->flat = true;
+        return ACLZ_OK;
+    }
+    Pieces pc;
+    if (int rc = make_pieces(h, st, 1 << 30, pc)) return rc;
+    Dev &defscan = pc.defscan, &P = pc.P, &owner = pc.owner, &off = pc.off, &dmk = pc.dmk;
+    const uint64_t np = pc.np;
+    const unsigned long long def_bytes = pc.def_bytes;
     // the two-wave schedule: triplets, per-block segments, pending bits
     Dev tri, bflag, seg, pending, done;
     FCK(cudaMalloc(&tri.p, 16 * np));
@@ -336,4 +362,93 @@ extern "C" int aclz_flatten(aclz_handle *h, void *stream) {
     h->mean_deferred_len = (double)def_bytes / (double)np;
     h->flat = true;
     return aclz_set_range_bytes(h, h->range_bytes, stream);
+}
+
+// ------------------------------------------------------------- reshape
+//
+// Shorter chains for the wavefront schedule itself: a few doubling rounds,
+// then every deferred match is written back as consecutive tokens, one per
+// piece (the first keeps the match's literal run, the others have none), and
+// the decode index (minimal tags, worklists, persistent schedule) is rebuilt
+// for the new token array.  Each piece copies the same bytes from an earlier
+// copy of them, so its source still lies strictly before it and within the
+// stream; the thresholds by distance class no longer hold for the new
+// tokens, and the decode does not need them.
+
+namespace {
+
+__global__ void k_rs_count(const uint4 *__restrict__ tok, const uint32_t *__restrict__ defscan,
+                           const uint64_t *__restrict__ off, uint64_t nt, uint32_t *cnt) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nt; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 tk = __ldg(tok + t);
+        if (tk.y && (tk.w >> 8)) {
+            const uint32_t q = defscan[t];
+            cnt[t] = (uint32_t)(off[q + 1] - off[q]);
+        } else {
+            cnt[t] = 1u;
+        }
+    }
+}
+
+__global__ void k_rs_emit(const uint4 *__restrict__ tok, const uint32_t *__restrict__ defscan,
+                          const uint64_t *__restrict__ off, const uint4 *__restrict__ P,
+                          const uint32_t *__restrict__ pos, uint64_t nt, uint4 *tok2) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nt; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 tk = __ldg(tok + t);
+        uint64_t w = pos[t];
+        if (tk.y && (tk.w >> 8)) {
+            const uint32_t q = defscan[t];
+            for (uint64_t j = off[q]; j < off[q + 1]; j++, w++) {
+                const uint4 p = P[j];
+                tok2[w] = make_uint4(j == off[q] ? tk.x : 0u, p.y, p.z, p.w & 0xffu);
+            }
+        } else {
+            tok2[w] = make_uint4(tk.x, tk.y, tk.z, tk.w & 0xffu);
+        }
+    }
+}
+
+__global__ void k_rs_blk(const uint64_t *__restrict__ blk_tok, const uint32_t *__restrict__ pos, uint32_t nb,
+                         uint64_t nt2, uint64_t *blk_tok2) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= nb; b += gridDim.x * blockDim.x)
+        blk_tok2[b] = b < nb ? pos[blk_tok[b]] : nt2;
+}
+
+}  // namespace
+
+extern "C" int aclz_reshape(aclz_handle *h, uint32_t rounds, void *stream) {
+    if (!h || h->flat) return ACLZ_E_INVAL;
+    if (rounds == 0 || h->n_deferred == 0) return ACLZ_OK;
+    if (rounds > 32) return ACLZ_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t nt = h->n_tokens;
+    const uint32_t nb = h->n_blocks;
+    Pieces pc;
+    if (int rc = make_pieces(h, st, (int)rounds, pc)) return rc;
+    Dev cnt, tok2, blk2;
+    FCK(cudaMalloc(&cnt.p, 4 * (nt + 1)));
+    k_rs_count<<<grid_for(nt), 256, 0, st>>>((const uint4 *)h->d_tok, pc.defscan.as<uint32_t>(), pc.off.as<uint64_t>(),
+                                              nt, cnt.as<uint32_t>());
+    FCK(cudaGetLastError());
+    if (int rc = device_excl_scan(cnt.as<uint32_t>(), nt, cnt.as<uint32_t>() + nt, st)) return rc;
+    uint32_t nt2 = 0;
+    FCK(cudaMemcpyAsync(&nt2, cnt.as<uint32_t>() + nt, 4, cudaMemcpyDeviceToHost, st));
+    FCK(cudaStreamSynchronize(st));
+    if (nt2 >= 0xfffffff0u) return ACLZ_E_UNSUPPORTED;
+    FCK(cudaMalloc(&tok2.p, 16 * (uint64_t)nt2));
+    FCK(cudaMalloc(&blk2.p, 8 * ((uint64_t)nb + 1)));
+    k_rs_emit<<<grid_for(nt), 256, 0, st>>>((const uint4 *)h->d_tok, pc.defscan.as<uint32_t>(), pc.off.as<uint64_t>(),
+                                             pc.P.as<uint4>(), cnt.as<uint32_t>(), nt, tok2.as<uint4>());
+    k_rs_blk<<<grid_for(nb + 1), 256, 0, st>>>(h->d_blk_tok, cnt.as<uint32_t>(), nb, nt2, blk2.as<uint64_t>());
+    FCK(cudaGetLastError());
+    FCK(cudaStreamSynchronize(st));
+    cudaFree(h->d_tok);
+    cudaFree(h->d_blk_tok);
+    h->d_tok = tok2.p;
+    tok2.p = nullptr;
+    h->d_blk_tok = blk2.as<uint64_t>();
+    blk2.p = nullptr;
+    h->n_tokens = nt2;
+    h->flags &= (uint16_t)~kFlagWaves;
+    return build_index(h, false, 0, false, stream);
 }

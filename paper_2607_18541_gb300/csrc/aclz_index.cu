@@ -561,64 +561,31 @@ int aclz::device_excl_scan(uint32_t *d, uint64_t n, uint32_t *d_total, void *str
     return cuda_rc(cudaGetLastError());
 }
 
-extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_handle **out) {
-    return aclz_upload_ex(host_buf, n, 0, stream, out);
-}
-
-extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out) {
-    if (flags & ~(uint32_t)ACLZ_UPLOAD_FLATTEN) return ACLZ_E_INVAL;
-    const bool flat_up = (flags & ACLZ_UPLOAD_FLATTEN) != 0;
-    if (!host_buf || !out) return ACLZ_E_INVAL;
-    *out = nullptr;
-    View v;
-    int rc = parse_container((const uint8_t *)host_buf, n, &v, true);
-    if (rc) return rc;
-    if (!is_pow2(v.block_size) || v.block_size < kMinBlock || v.block_size > kMaxBlock)
-        return ACLZ_E_UNSUPPORTED;
-    if (v.n_tokens >= 0xffffffffULL) return ACLZ_E_UNSUPPORTED;
-    cudaStream_t st = (cudaStream_t)stream;
-    aclz_handle *h = new aclz_handle();
-    auto cleanup = [&]() { aclz_free(h); };
-    cudaGetDevice(&h->device);
-    h->total_len = v.total_len;
-    h->n_tokens = v.n_tokens;
-    h->n_literals = v.n_literals;
-    h->block_size = v.block_size;
-    h->log2_bs = log2u(v.block_size);
-    h->n_blocks = v.n_blocks;
-    h->flags = v.flags;
-    std::memcpy(h->mm, v.mm, 4);
-    const uint32_t nb = v.n_blocks;
-    const uint64_t nt = v.n_tokens;
-    // directory -> (nb + 1) offset arrays
-    std::vector<uint64_t> bt(nb + 1), bl(nb + 1);
-    for (uint32_t b = 0; b < nb; b++) {
-        bt[b] = rd64(v.dir + (uint64_t)kDirent * b);
-        bl[b] = rd64(v.dir + (uint64_t)kDirent * b + 8);
+// Decode index of h from its device tokens (d_tok with n_tokens entries,
+// d_blk_tok, d_blk_lit, d_lit): per-token validation and offsets, wave
+// tags (given ones checked, else minimal ones; local 0/1 ones for the
+// flattened schedule), worklist slots and the persistent schedule.
+// Allocates d_tokdst, d_toklit, d_slot and the schedule arrays (freed first
+// when present).  Synchronizes the stream.
+int aclz::build_index(aclz_handle *h, bool has_tags, uint32_t given_waves, bool flat_local, void *stream_) {
+    auto cleanup = []() {};
+    void *stream = stream_;
+    cudaStream_t st = (cudaStream_t)stream_;
+    const bool flat_up = flat_local;
+    const uint32_t nb = h->n_blocks;
+    const uint64_t nt = h->n_tokens;
+    int rc = ACLZ_OK;
+    for (void **pp : {(void **)&h->d_tokdst, (void **)&h->d_toklit, (void **)&h->d_slot, &h->d_tri, &h->d_seg,
+                      &h->d_ranges, (void **)&h->d_pending, (void **)&h->d_done}) {
+        if (*pp) cudaFree(*pp);
+        *pp = nullptr;
     }
-    bt[nb] = nt;
-    bl[nb] = v.n_literals;
-    CK(cudaMalloc(&h->d_tok, kTok * (nt ? nt : 1)));
-    CK(cudaMalloc((void **)&h->d_lit, v.n_literals + 32));
-    CK(cudaMalloc((void **)&h->d_blk_tok, 8 * (nb + 1)));
-    CK(cudaMalloc((void **)&h->d_blk_lit, 8 * (nb + 1)));
+    h->n_seg = h->n_ranges = 0;
+    h->n_deferred = 0;
     CK(cudaMalloc((void **)&h->d_tokdst, 4 * (nt ? nt : 1)));
     CK(cudaMalloc((void **)&h->d_toklit, 4 * (nt ? nt : 1)));
     CK(cudaMalloc((void **)&h->d_slot, 4 * (nt ? nt : 1)));
-    CK(cudaMalloc((void **)&h->d_err, 64));
     CK(cudaMemsetAsync(h->d_err, 0, 64, st));
-    CK(cudaMemsetAsync(h->d_lit + v.n_literals, 0, 32, st));
-    if (nt) CK(cudaMemcpyAsync(h->d_tok, v.tok, kTok * nt, cudaMemcpyHostToDevice, st));
-    if (v.n_literals) CK(cudaMemcpyAsync(h->d_lit, v.lit, v.n_literals, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(h->d_blk_tok, bt.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(h->d_blk_lit, bl.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, st));
-    if (nb == 0) {
-        h->n_waves = 0;
-        h->wave_start.assign(1, 0);
-        CK(cudaStreamSynchronize(st));
-        *out = h;
-        return ACLZ_OK;
-    }
     // scratch words: [0] err (handle), work: maxtag, counter, total, first_bad
     DevBuf work;
     CK(cudaMalloc(&work.p, 64));
@@ -629,10 +596,9 @@ extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, 
     CK(cudaMemsetAsync(work.p, 0, 32, st));
     CK(cudaMemsetAsync(d_first_bad, 0xff, 8, st));
     const unsigned wblocks = (nb + 7) / 8;  // 8 warps per CTA
-    const bool has_tags = (v.flags & kFlagWaves) != 0;
-    k_index_scan<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_blk_lit,
-                                           h->d_tokdst, h->d_toklit, nb, h->log2_bs, v.total_len, has_tags,
-                                           h->d_err, d_first_bad);
+    k_index_scan<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_blk_lit, h->d_tokdst,
+                                           h->d_toklit, nb, h->log2_bs, h->total_len, has_tags, h->d_err,
+                                           d_first_bad);
     CK(cudaGetLastError());
     uint32_t herr = 0;
     CK(cudaMemcpyAsync(&herr, h->d_err, 4, cudaMemcpyDeviceToHost, st));
@@ -673,7 +639,7 @@ extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, 
     if (hw[1]) { cleanup(); return ACLZ_E_CORRUPT; }
     const uint32_t maxtag = hw[0];
     if (maxtag > kMaxWave) { cleanup(); return ACLZ_E_UNSUPPORTED; }
-    if (has_tags && v.n_waves != maxtag + 1) { cleanup(); return ACLZ_E_CORRUPT; }
+    if (has_tags && given_waves != maxtag + 1) { cleanup(); return ACLZ_E_CORRUPT; }
     h->n_waves = maxtag + 1;
     h->wave_start.assign(h->n_waves + 1, 0);
     CK(cudaMemsetAsync(h->d_slot, 0xff, 4 * nt, st));
@@ -739,6 +705,66 @@ extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, 
     }
     CK(cudaMalloc((void **)&h->d_done, 8 * (size_t)nb * h->n_wave_words));
     CK(cudaStreamSynchronize(st));
+    return ACLZ_OK;
+}
+
+extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_handle **out) {
+    return aclz_upload_ex(host_buf, n, 0, stream, out);
+}
+
+extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out) {
+    if (flags & ~(uint32_t)ACLZ_UPLOAD_FLATTEN) return ACLZ_E_INVAL;
+    const bool flat_up = (flags & ACLZ_UPLOAD_FLATTEN) != 0;
+    if (!host_buf || !out) return ACLZ_E_INVAL;
+    *out = nullptr;
+    View v;
+    int rc = parse_container((const uint8_t *)host_buf, n, &v, true);
+    if (rc) return rc;
+    if (!is_pow2(v.block_size) || v.block_size < kMinBlock || v.block_size > kMaxBlock)
+        return ACLZ_E_UNSUPPORTED;
+    if (v.n_tokens >= 0xffffffffULL) return ACLZ_E_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    aclz_handle *h = new aclz_handle();
+    auto cleanup = [&]() { aclz_free(h); };
+    cudaGetDevice(&h->device);
+    h->total_len = v.total_len;
+    h->n_tokens = v.n_tokens;
+    h->n_literals = v.n_literals;
+    h->block_size = v.block_size;
+    h->log2_bs = log2u(v.block_size);
+    h->n_blocks = v.n_blocks;
+    h->flags = v.flags;
+    std::memcpy(h->mm, v.mm, 4);
+    const uint32_t nb = v.n_blocks;
+    const uint64_t nt = v.n_tokens;
+    // directory -> (nb + 1) offset arrays
+    std::vector<uint64_t> bt(nb + 1), bl(nb + 1);
+    for (uint32_t b = 0; b < nb; b++) {
+        bt[b] = rd64(v.dir + (uint64_t)kDirent * b);
+        bl[b] = rd64(v.dir + (uint64_t)kDirent * b + 8);
+    }
+    bt[nb] = nt;
+    bl[nb] = v.n_literals;
+    CK(cudaMalloc(&h->d_tok, kTok * (nt ? nt : 1)));
+    CK(cudaMalloc((void **)&h->d_lit, v.n_literals + 32));
+    CK(cudaMalloc((void **)&h->d_blk_tok, 8 * (nb + 1)));
+    CK(cudaMalloc((void **)&h->d_blk_lit, 8 * (nb + 1)));
+    CK(cudaMalloc((void **)&h->d_err, 64));
+    CK(cudaMemsetAsync(h->d_err, 0, 64, st));
+    CK(cudaMemsetAsync(h->d_lit + v.n_literals, 0, 32, st));
+    if (nt) CK(cudaMemcpyAsync(h->d_tok, v.tok, kTok * nt, cudaMemcpyHostToDevice, st));
+    if (v.n_literals) CK(cudaMemcpyAsync(h->d_lit, v.lit, v.n_literals, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->d_blk_tok, bt.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->d_blk_lit, bl.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, st));
+    if (nb == 0) {
+        h->n_waves = 0;
+        h->wave_start.assign(1, 0);
+        CK(cudaStreamSynchronize(st));
+        *out = h;
+        return ACLZ_OK;
+    }
+    rc = build_index(h, (v.flags & kFlagWaves) != 0, v.n_waves, flat_up, stream);
+    if (rc) { cleanup(); return rc; }
     if (flat_up) {
         rc = aclz_flatten(h, stream);
         if (rc) { cleanup(); return rc; }

@@ -59,6 +59,16 @@ void note_cuda_error(int cuda_error_code);
 // (device); stream-ordered, temporary storage allocated on the stream.
 int device_excl_scan(uint32_t *d, uint64_t n, uint32_t *d_total, void *stream);
 
+}  // namespace aclz
+
+struct aclz_handle;
+
+namespace aclz {
+
+// Decode index of h from its device tokens (validation, offsets, wave tags,
+// worklists, schedule); see aclz_index.cu.
+int build_index(aclz_handle *h, bool has_tags, uint32_t given_waves, bool flat_local, void *stream);
+
 // Matches per work range for a target byte size of deferred matches.
 inline uint32_t range_matches(uint32_t range_bytes, double mean_len) {
     double t = mean_len > 0 ? (double)range_bytes / mean_len : 16.0;

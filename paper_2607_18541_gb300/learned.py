@@ -43,6 +43,7 @@ FALLBACK = CANDIDATES.index((12, 16, 24, 32))
 BASE = CANDIDATES.index((6, 8, 10, 12))
 BLOCK = 1 << 14
 N_FEATURES = 24
+TOKEN_TARGET = 0.95  # training labels aim at 5% fewer tokens than 12/16/24/32
 DIST = (128, 16384, 2097152)
 
 
@@ -192,18 +193,34 @@ def features(x, base_container, block_size: int = BLOCK, stream=None) -> np.ndar
 
 
 def label_data(x, block_size: int = BLOCK, threads: int = 0):
-    """Features and labels of one training stream; also the per-candidate
-    block costs and token counts."""
+    """Features of one training stream and, per candidate, its block costs
+    and token counts [K, n_blocks]."""
     threads = threads or min(K, os.cpu_count() or 1)
     per = max(1, (os.cpu_count() or 1) // threads)
     with ThreadPoolExecutor(threads) as ex:
         cs = list(ex.map(lambda mm: encode(x, mm, block_size=block_size, threads=per), CANDIDATES))
-    costs = np.stack([block_costs(c) for c in cs])          # [K, nb]
+    costs = np.stack([block_costs(c) for c in cs])
     ntok = np.stack([read_tokens(c)[0].astype(np.float64) for c in cs])
-    ok = costs <= costs[FALLBACK][None, :] + 1e-9
-    key = np.where(ok, ntok + costs / (1.0 + costs.max()), np.inf)
-    y = np.argmin(key, axis=0).astype(np.int32)
-    return features(x, cs[BASE], block_size), y, costs, ntok
+    return features(x, cs[BASE], block_size), costs, ntok
+
+
+def lagrange_labels(costs, ntok, token_target: float = TOKEN_TARGET):
+    """Per-block labels trading size against tokens (the decode-speed lever):
+    k(b) = argmin_k cost[k, b] + lam * tokens[k, b], with lam >= 0 the
+    smallest price per token at which the stream's total tokens fall to
+    token_target x those of 12/16/24/32 (bisection)."""
+    nb = costs.shape[1]
+    want = token_target * ntok[FALLBACK].sum()
+    lo, hi = 0.0, 1.0
+    while ntok[np.argmin(costs + hi * ntok, axis=0), np.arange(nb)].sum() > want and hi < 1e6:
+        hi *= 2.0
+    for _ in range(50):
+        lam = 0.5 * (lo + hi)
+        if ntok[np.argmin(costs + lam * ntok, axis=0), np.arange(nb)].sum() > want:
+            lo = lam
+        else:
+            hi = lam
+    return np.argmin(costs + hi * ntok, axis=0).astype(np.int32), hi
 
 
 class Model:
@@ -284,38 +301,50 @@ class Model:
         return m
 
 
-def encode_learned(model: Model, x, block_size: int = BLOCK, tau: float = 0.0, passes: int = 3,
+def encode_learned(model: Model, x, block_size: int = BLOCK, tau: float = 0.0, passes: int = 6,
                    base=None, fb=None):
-    """Per-block thresholds from the network, judged against the fixed
-    12/16/24/32 encode: a block keeps the network's pick only where it has no
-    more tokens (the decode-speed lever) and no higher cost than under the
-    fallback.  A block's parse depends only on its own thresholds, so token
-    counts are exact; costs use stream-wide frequencies, so the check is
-    repeated, and if the whole-stream estimate still exceeds the fallback's
-    the fallback container is returned.  base / fb: the containers at
-    6/8/10/12 and 12/16/24/32 if already encoded.  Returns (container,
-    choices)."""
+    """Per-block thresholds from the network, judged by the plain encoder's
+    ratio and decode speed: the result is kept only if its estimated size
+    and its token count (the decode-speed lever, Sec. III-C) are both no
+    larger than the fixed 12/16/24/32 encode's.  When one is larger, the
+    least efficient picks (largest size increase per token saved, or
+    largest token increase per byte saved) are put back to 12/16/24/32
+    until the excess is covered, and the stream is encoded again (a block's
+    parse depends only on its own thresholds; sizes use stream-wide symbol
+    frequencies).  After `passes` tries the fallback container is returned.
+    base / fb: the containers at 6/8/10/12 and 12/16/24/32 if already
+    encoded.  Returns (container, choices)."""
     if base is None:
         base = encode(x, CANDIDATES[BASE], block_size=block_size)
     if fb is None:
         fb = encode(x, CANDIDATES[FALLBACK], block_size=block_size)
     fb_cost = block_costs(fb)
-    fb_tok = read_tokens(fb)[0]
-    fb_est = est_bytes(fb)
+    fb_tok = read_tokens(fb)[0].astype(np.int64)
+    fb_est, fb_T = est_bytes(fb), int(fb_tok.sum())
     k = model.choose(features(x, base, block_size), tau)
-    for i in range(passes + 1):
+    for _ in range(passes):
         if np.all(k == FALLBACK):
-            return fb, k
+            break
         bmm = np.array([CANDIDATES[j] for j in k], dtype=np.uint8)
         c = encode(x, block_mm=bmm, block_size=block_size)
-        worse = (k != FALLBACK) & ((block_costs(c) > fb_cost + 1e-9) | (read_tokens(c)[0] > fb_tok))
-        if not worse.any():
-            if est_bytes(c) <= fb_est:
-                return c, k
-            break
-        if i == passes:
-            break
-        k[worse] = FALLBACK
+        tok = read_tokens(c)[0].astype(np.int64)
+        est, T = est_bytes(c), int(tok.sum())
+        if est <= fb_est and T <= fb_T:
+            return c, k
+        dc = block_costs(c) - fb_cost          # bytes added by each block's pick
+        dt = (tok - fb_tok).astype(np.float64)  # tokens added
+        picked = np.nonzero(k != FALLBACK)[0]
+        if est > fb_est:
+            # least bytes-efficient picks first: most bytes per token saved
+            key = dc[picked] / np.maximum(1.0, -dt[picked])
+            need = (est - fb_est) * 1.2 + 1.0
+        else:
+            key = dt[picked] / np.maximum(1.0, -dc[picked])
+            need = (T - fb_T) * 1.2 + 1.0
+        order = picked[np.argsort(-key)]
+        gain = dc[order] if est > fb_est else dt[order]
+        cut = int(np.searchsorted(np.cumsum(np.maximum(gain, 0.0)), need)) + 1
+        k[order[:cut]] = FALLBACK
     k[:] = FALLBACK
     return fb, k
 
@@ -350,7 +379,8 @@ def _decode_gbs(c, n: int, reps: int = 5, **cfg):
 def train_default(scale: int = 1, steps: int = 2000, seed: int = 20260712, log=print):
     feats, labels = [], []
     for s in training_streams(scale):
-        f, y, _, _ = label_data(s)
+        f, costs, ntok = label_data(s)
+        y, _ = lagrange_labels(costs, ntok)
         feats.append(f)
         labels.append(y)
     f = np.concatenate(feats)
@@ -363,7 +393,18 @@ def train_default(scale: int = 1, steps: int = 2000, seed: int = 20260712, log=p
     return model
 
 
-def gain_single(model: Model, x, block_size: int = BLOCK, reps: int = 5):
+class Choices:
+    """Known per-block choices in the place of the network (the label bound
+    of a stream: its own Lagrangian labels, through the same judge)."""
+
+    def __init__(self, k):
+        self.k = np.asarray(k)
+
+    def choose(self, f, tau: float = 0.0):
+        return self.k.copy()
+
+
+def gain_single(model: Model, x, block_size: int = BLOCK, reps: int = 5, bound: bool = True):
     """One stream at 6/8/10/12, 12/16/24/32 and learned per-block thresholds:
     estimated ratio, tokens and decode GB/s (AUTO mode), output checked."""
     import torch
@@ -372,12 +413,17 @@ def gain_single(model: Model, x, block_size: int = BLOCK, reps: int = 5):
     base = encode(x, CANDIDATES[BASE], block_size=block_size)
     fb = encode(x, CANDIDATES[FALLBACK], block_size=block_size)
     lc, k = encode_learned(model, x, block_size, base=base, fb=fb)
-    for name, c in (("6/8/10/12", base), ("12/16/24/32", fb), ("learned", lc)):
+    rows_c = [("6/8/10/12", base), ("12/16/24/32", fb), ("learned", lc)]
+    if bound:
+        _, costs, ntok = label_data(x, block_size)
+        yb, _ = lagrange_labels(costs, ntok)
+        rows_c.append(("label bound", encode_learned(Choices(yb), x, block_size, base=base, fb=fb)[0]))
+    for name, c in rows_c:
         gbs, out = _decode_gbs(c, x.size, reps)
         rows.append(dict(thresholds=name, bytes=int(x.size), est_ratio=round(x.size / est_bytes(c), 4),
                          tokens=int(read_tokens(c)[0].sum()), decode_gbs=round(gbs, 1),
                          exact=bool(torch.equal(out, xd))))
-    rows[-1]["choices"] = np.bincount(k, minlength=K).tolist()
+    rows[2]["choices"] = np.bincount(k, minlength=K).tolist()
     return rows
 
 
@@ -421,7 +467,8 @@ def main():
     if a.save:
         model.save(a.save)
     for name, x in (("fastq", synth.fastq(a.fastq_mib << 20, seed=0x7A1000)),
-                    ("markov", synth.markov2(a.markov_mib << 20, seed=0x7B1000))):
+                    ("markov", synth.markov2(a.markov_mib << 20, seed=0x7B1000)),
+                    ("text", synth.wordtext(a.markov_mib << 20, seed=0x7C1000))):
         for r in gain_single(model, x):
             print(json.dumps(dict(workload=name, **r)), flush=True)
     for r in gain_batched(model, a.streams):

@@ -334,6 +334,44 @@ def test_flatten_upload_without_tags(kind):
         aclz.aclz_free(h)
 
 
+@pytest.mark.parametrize("kind", ["sweep1024", "sweep32", "fastq_base", "text_tuned", "tiny_blocks"])
+@pytest.mark.parametrize("rounds", [1, 2])
+def test_reshape_cuts_waves_and_decodes_identically(kind, rounds):
+    c = _flatten_case(kind)
+    exp = oracle.decode(c)
+    fe = oracle.fnv_chunked(exp)
+    s = torch.cuda.current_stream()
+    h = aclz.aclz_upload(c, s)
+    try:
+        i0 = aclz.aclz_handle_info(h)
+        aclz.aclz_reshape(h, rounds, s)
+        i1 = aclz.aclz_handle_info(h)
+        assert i1.n_tokens >= i0.n_tokens and i1.total_len == i0.total_len
+        assert i1.n_waves <= i0.n_waves
+        if i0.n_waves > 8:
+            assert i1.n_waves < i0.n_waves
+        assert aclz.aclz_tags(h).size == i1.n_tokens
+        out = torch.empty(len(exp) + 16, dtype=torch.uint8, device="cuda")
+        for mode, flags in MODES:
+            out.zero_()
+            aclz.aclz_decode_all(h, out, mode=mode, flags=flags, stream=s)
+            assert aclz.aclz_device_status(h, s) == 0
+            assert np.array_equal(out[:len(exp)].cpu().numpy(), exp), (mode, flags)
+        assert aclz.aclz_fnv(out, len(exp), stream=s) == fe
+        lo, hi = len(exp) // 5, min(len(exp), len(exp) // 5 + 300_000)
+        part = torch.empty(hi - lo + 16, dtype=torch.uint8, device="cuda")
+        aclz.aclz_decode_range(h, lo, hi, part, stream=s)
+        assert np.array_equal(part[:hi - lo].cpu().numpy(), exp[lo:hi])
+        # and flattening after reshaping still decodes the bytes
+        aclz.aclz_flatten(h, s)
+        aclz.aclz_decode_all(h, out, stream=s)
+        assert np.array_equal(out[:len(exp)].cpu().numpy(), exp)
+        with pytest.raises(aclz.AclzError):
+            aclz.aclz_reshape(h, 1, s)
+    finally:
+        aclz.aclz_free(h)
+
+
 def test_upload_ex_rejects_unknown_flags():
     c = _flatten_case("markov_base")
     with pytest.raises(aclz.AclzError):

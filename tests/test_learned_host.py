@@ -109,3 +109,66 @@ def test_per_block_thresholds_encode_like_the_oracle(mixed):
     want = oracle.strip_tags(oracle.encode(mixed, bs, block_mm=bmm, chain_depth=16))
     assert np.array_equal(got, want)
     assert np.array_equal(oracle.decode(got), mixed)
+
+
+def test_lagrange_labels_meet_the_token_target_with_the_smallest_price():
+    rng = np.random.default_rng(5)
+    K, nb = learned.K, 400
+    ntok = rng.integers(5, 60, (K, nb)).astype(np.float64)
+    costs = rng.uniform(100, 1000, (K, nb))
+    for target in (1.0, 0.95, 0.8):
+        y, lam = learned.lagrange_labels(costs, ntok, target)
+        want = target * ntok[learned.FALLBACK].sum()
+        got = ntok[y, np.arange(nb)].sum()
+        assert got <= want + 1e-9
+        # each label minimises cost + lam * tokens on its block
+        assert np.array_equal(y, np.argmin(costs + lam * ntok, axis=0))
+        # a slightly lower price misses the target (lam is the smallest)
+        if lam > 1e-6:
+            y2 = np.argmin(costs + 0.99 * lam * ntok, axis=0)
+            assert ntok[y2, np.arange(nb)].sum() > want - 1e-9
+
+
+def test_lagrange_labels_at_zero_price_take_the_smallest_blocks():
+    costs = np.array([[1.0, 5.0], [2.0, 1.0]] + [[9.0, 9.0]] * (learned.K - 2))
+    ntok = np.ones_like(costs)
+    y, lam = learned.lagrange_labels(costs, ntok, 1.0)
+    assert lam < 1e-6 and list(y) == [0, 1]
+
+
+class _FixedChoices:
+    """Stands in for the trained network: returns given per-block choices."""
+
+    def __init__(self, k):
+        self.k = np.asarray(k)
+
+    def choose(self, f, tau=0.0):
+        return self.k.copy()
+
+
+@pytest.mark.parametrize("kind", ["lagrange", "all_push", "all_base"])
+def test_judge_never_returns_a_larger_or_slower_encode(monkeypatch, mixed, kind):
+    bs = 1 << 14
+    nb = -(-mixed.size // bs)
+    monkeypatch.setattr(learned, "features", lambda x, base, block_size=bs: np.zeros((nb, learned.N_FEATURES)))
+    if kind == "lagrange":
+        _, costs, ntok = (None,) + tuple(
+            np.stack(v) for v in zip(*[(learned.block_costs(c), learned.read_tokens(c)[0].astype(float))
+                                       for c in (learned.encode(mixed, mm, block_size=bs)
+                                                 for mm in learned.CANDIDATES)]))
+        k, _ = learned.lagrange_labels(costs, ntok)
+    elif kind == "all_push":
+        k = np.full(nb, learned.CANDIDATES.index((16, 24, 32, 48)))
+    else:
+        k = np.full(nb, learned.BASE)
+    c, kk = learned.encode_learned(_FixedChoices(k), mixed, block_size=bs)
+    fb = learned.encode(mixed, learned.CANDIDATES[learned.FALLBACK], block_size=bs)
+    assert learned.est_bytes(c) <= learned.est_bytes(fb)
+    assert learned.read_tokens(c)[0].sum() <= learned.read_tokens(fb)[0].sum()
+    assert np.array_equal(oracle.decode(c), mixed)
+    # the container's tokens are exactly those of the returned choices
+    bmm = np.array([learned.CANDIDATES[j] for j in kk], dtype=np.uint8)
+    want = learned.read_tokens(learned.encode(mixed, block_mm=bmm, block_size=bs))
+    got = learned.read_tokens(c)
+    for a, b in zip(got[:5], want[:5]):
+        assert np.array_equal(a, b)
