@@ -105,17 +105,24 @@ def kernel_sources_sha() -> str:
 
 
 def recorded_traffic(workload: str):
-    """dram bytes per step from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary (profiles/traffic_k_ranges_<workload>.txt, lines "key: value"),
+    if it was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", f"traffic_k_ranges_{workload}.txt")
     if not os.path.exists(p):
         return None
+    d = {}
     with open(p) as f:
-        d = json.load(f)
-    e = d.get(workload)
-    if not e or e.get("kernel_sources_sha") != kernel_sources_sha():
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                d[k.strip()] = v.strip()
+    if d.get("kernel_sources_sha") != kernel_sources_sha():
         return None
-    return e.get("dram_bytes_per_step")
+    try:
+        return int(d["dram_bytes_read"]) + int(d["dram_bytes_write"])
+    except (KeyError, ValueError):
+        return None
 
 
 class ClockSampler:
