@@ -141,6 +141,16 @@ int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_handle **ou
 #define ACLZ_UPLOAD_FLATTEN 1u
 int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out);
 
+/* Write the handle's stream back as a host container, with the wave tags
+ * the upload computed (flag and n_waves set, per-block max wave in the
+ * directory), so a later upload of it only checks the tags, in parallel,
+ * instead of computing them in block order.  The container format and the
+ * tags are those the encoder could have written (Sec. I: the wavefront's
+ * waves); a reshaped handle exports its rewritten tokens.  host_out NULL:
+ * only *out_size.  ACLZ_E_CAPACITY when cap is too small, ACLZ_E_INVAL for
+ * a flattened handle (its 0/1 tags are not a legal wave tagging). */
+int aclz_export(const aclz_handle *h, void *host_out, uint64_t cap, uint64_t *out_size);
+
 /* Free a handle and its device memory (after its work has completed). */
 int aclz_free(aclz_handle *h);
 

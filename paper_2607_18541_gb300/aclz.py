@@ -87,6 +87,7 @@ _SIGS = [
     ("aclz_tags", _I, [_VP, _U32P, _U64]),
     ("aclz_set_range_bytes", _I, [_VP, _U32, _VP]),
     ("aclz_flatten", _I, [_VP, _VP]),
+    ("aclz_export", _I, [_VP, _VP, _U64, _U64P]),
     ("aclz_reshape", _I, [_VP, _U32, _VP]),
     ("aclz_decode_all", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP]),
     ("aclz_decode_all_ev", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP, _VP]),
@@ -260,6 +261,15 @@ def aclz_tags(h: int) -> np.ndarray:
     out = np.zeros(max(1, nt), dtype=np.uint32)
     _ck(lib().aclz_tags(h, out.ctypes.data_as(_U32P), nt), "aclz_tags")
     return out[:nt]
+
+
+def aclz_export(h: int) -> np.ndarray:
+    """The handle's stream as a host container carrying its wave tags."""
+    size = ctypes.c_uint64(0)
+    _ck(lib().aclz_export(h, None, 0, ctypes.byref(size)), "aclz_export")
+    out = np.empty(size.value, dtype=np.uint8)
+    _ck(lib().aclz_export(h, _hptr(out), out.size, ctypes.byref(size)), "aclz_export")
+    return out
 
 
 def aclz_flatten(h: int, stream=None) -> None:

@@ -851,3 +851,53 @@ extern "C" int aclz_set_range_bytes(aclz_handle *h, uint32_t range_bytes, void *
     cudaFree(rflag);
     return rc;
 }
+
+extern "C" int aclz_export(const aclz_handle *h, void *host_out, uint64_t cap, uint64_t *out_size) {
+    if (!h || !out_size || h->flat) return ACLZ_E_INVAL;
+    const uint64_t nt = h->n_tokens, nl = h->n_literals;
+    const uint32_t nb = h->n_blocks;
+    const uint64_t need = kHdr + (uint64_t)kDirent * nb + (uint64_t)kTok * nt + nl;
+    *out_size = need;
+    if (!host_out) return ACLZ_OK;
+    if (cap < need) return ACLZ_E_CAPACITY;
+    uint8_t *c = (uint8_t *)host_out;
+    uint8_t *dir = c + kHdr, *tok = dir + (uint64_t)kDirent * nb, *lit = tok + (uint64_t)kTok * nt;
+    std::vector<uint64_t> bt(nb + 1), bl(nb + 1);
+    cudaError_t e = cudaSuccess;
+    if (nb) {
+        e = cudaMemcpy(bt.data(), h->d_blk_tok, 8 * ((size_t)nb + 1), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(bl.data(), h->d_blk_lit, 8 * ((size_t)nb + 1), cudaMemcpyDeviceToHost);
+    }
+    if (e == cudaSuccess && nt) e = cudaMemcpy(tok, h->d_tok, kTok * nt, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && nl) e = cudaMemcpy(lit, h->d_lit, nl, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        return ACLZ_E_CUDA;
+    }
+    const bool tagged = h->n_waves > 0;
+    std::memset(c, 0, kHdr);
+    c[0] = 'A'; c[1] = 'C'; c[2] = 'L'; c[3] = 'Z';
+    wr16(c + 4, 1);
+    wr16(c + 6, tagged ? kFlagWaves : 0);
+    wr64(c + 8, h->total_len);
+    wr32(c + 16, h->block_size);
+    wr32(c + 20, nb);
+    wr64(c + 24, nt);
+    wr64(c + 32, nl);
+    wr32(c + 40, tagged ? h->n_waves : 0);
+    std::memcpy(c + 44, h->mm, 4);
+    const uint32_t bounds[3] = {128, 16384, 2097152};
+    for (int i = 0; i < 3; i++) wr32(c + 48 + 4 * i, bounds[i]);
+    for (uint32_t b = 0; b < nb; b++) {
+        uint8_t *d = dir + (uint64_t)kDirent * b;
+        std::memset(d, 0, kDirent);
+        wr64(d, bt[b]);
+        wr64(d + 8, bl[b]);
+        wr32(d + 16, (uint32_t)(bt[b + 1] - bt[b]));
+        uint32_t mw = 0;
+        for (uint64_t t = bt[b]; t < bt[b + 1]; t++) mw = std::max(mw, rd32(tok + kTok * t + 12) >> 8);
+        wr16(d + 20, (uint16_t)std::min<uint32_t>(mw, 0xffffu));
+        std::memcpy(d + 24, h->mm, 4);
+    }
+    return ACLZ_OK;
+}

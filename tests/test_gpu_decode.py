@@ -372,6 +372,39 @@ def test_reshape_cuts_waves_and_decodes_identically(kind, rounds):
         aclz.aclz_free(h)
 
 
+@pytest.mark.parametrize("kind", ["sweep1024", "fastq_base", "text_tuned"])
+def test_export_writes_the_minimal_tags_and_reuploads(kind):
+    c = oracle.strip_tags(_flatten_case(kind))
+    exp = oracle.decode(c)
+    mt, nw = oracle.min_tags(c)
+    s = torch.cuda.current_stream()
+    h = aclz.aclz_upload(c, s)
+    try:
+        e = aclz.aclz_export(h)
+    finally:
+        aclz.aclz_free(h)
+    hd = oracle.header(e)
+    assert hd.flags == 1 and hd.n_waves == nw
+    assert oracle.validate(e) == 0
+    assert np.array_equal(oracle.tokens(e)[4], mt)
+    assert np.array_equal(oracle.decode(e), exp)
+    h = aclz.aclz_upload(e, s)
+    try:
+        assert np.array_equal(aclz.aclz_tags(h), mt)
+        out = torch.empty(len(exp) + 16, dtype=torch.uint8, device="cuda")
+        aclz.aclz_decode_all(h, out, stream=s)
+        assert np.array_equal(out[:len(exp)].cpu().numpy(), exp)
+        # a reshaped handle exports its rewritten tokens, still a legal container
+        aclz.aclz_reshape(h, 1, s)
+        e2 = aclz.aclz_export(h)
+        assert oracle.validate(e2) == 0 and np.array_equal(oracle.decode(e2), exp)
+        aclz.aclz_flatten(h, s)
+        with pytest.raises(aclz.AclzError):
+            aclz.aclz_export(h)
+    finally:
+        aclz.aclz_free(h)
+
+
 def test_upload_ex_rejects_unknown_flags():
     c = _flatten_case("markov_base")
     with pytest.raises(aclz.AclzError):
