@@ -189,7 +189,8 @@ int aclz_flatten(aclz_handle *h, void *stream);
  * matches.  Decode and seek output are unchanged; aclz_handle_info then
  * reports the new token and wave counts and aclz_tags the new tags.
  * rounds 0 (or no deferred match) is a no-op; rounds > 32 or a flattened
- * handle: ACLZ_E_INVAL.  Synchronizes; no decode of h may be in flight. */
+ * handle: ACLZ_E_INVAL.  Synchronizes; no decode of h may be in flight.
+ * After any other error the handle is left part-way and must be freed. */
 int aclz_reshape(aclz_handle *h, uint32_t rounds, void *stream);
 
 /* Regroup the persistent schedule: consecutive (block, wave) segments are
