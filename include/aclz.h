@@ -137,7 +137,9 @@ int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_handle **ou
  * ordered pass over the blocks, so deep chains of copies do not slow the
  * upload, and aclz_tags returns these 0/1 tags.  A container with tags has
  * them checked as by aclz_upload first.  flags other than
- * ACLZ_UPLOAD_FLATTEN: ACLZ_E_INVAL. */
+ * ACLZ_UPLOAD_FLATTEN: ACLZ_E_INVAL.  Without the flag, an upload whose
+ * plain schedule would need more than 2^28 (wave, block) cells (copy chains
+ * thousands of waves deep) also flattens. */
 #define ACLZ_UPLOAD_FLATTEN 1u
 int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out);
 
@@ -148,7 +150,8 @@ int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *strea
  * tags are those the encoder could have written (Sec. I: the wavefront's
  * waves); a reshaped handle exports its rewritten tokens.  host_out NULL:
  * only *out_size.  ACLZ_E_CAPACITY when cap is too small, ACLZ_E_INVAL for
- * a flattened handle (its 0/1 tags are not a legal wave tagging). */
+ * a handle uploaded with ACLZ_UPLOAD_FLATTEN from an untagged container
+ * (its 0/1 tags are not a legal wave tagging). */
 int aclz_export(const aclz_handle *h, void *host_out, uint64_t cap, uint64_t *out_size);
 
 /* Free a handle and its device memory (after its work has completed). */

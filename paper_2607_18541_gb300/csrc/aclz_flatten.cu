@@ -234,9 +234,8 @@ struct Pieces {
 };
 
 int make_pieces(aclz_handle *h, cudaStream_t st, int max_rounds, Pieces &pc) {
-    const uint64_t nt = h->n_tokens, D = h->n_deferred;
+    const uint64_t nt = h->n_tokens;
     const uint32_t nb = h->n_blocks;
-    pc.D = D;
     // deferred matches in token order: defscan[t] = rank, defscan[nt] = D
     Dev work;
     FCK(cudaMalloc(&pc.defscan.p, 4 * (nt + 1)));
@@ -247,6 +246,12 @@ int make_pieces(aclz_handle *h, cudaStream_t st, int max_rounds, Pieces &pc) {
     k_is_deferred<<<grid_for(nt), 256, 0, st>>>((const uint4 *)h->d_tok, nt, pc.defscan.as<uint32_t>());
     FCK(cudaGetLastError());
     if (int rc = device_excl_scan(pc.defscan.as<uint32_t>(), nt, pc.defscan.as<uint32_t>() + nt, st)) return rc;
+    uint32_t d32 = 0;
+    FCK(cudaMemcpyAsync(&d32, pc.defscan.as<uint32_t>() + nt, 4, cudaMemcpyDeviceToHost, st));
+    FCK(cudaStreamSynchronize(st));
+    const uint64_t D = d32;
+    pc.D = D;
+    if (D == 0) return ACLZ_OK;
     // round 0: one piece per match
     uint64_t np = D;
     FCK(cudaMalloc(&pc.P.p, 16 * np));
@@ -308,14 +313,18 @@ extern "C" int aclz_flatten(aclz_handle *h, void *stream) {
     if (!h) return ACLZ_E_INVAL;
     if (h->flat) return ACLZ_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const uint64_t D = h->n_deferred;
     const uint32_t nb = h->n_blocks;
-    if (D == 0) {
+    if (nb == 0) {
         h->flat = true;
         return ACLZ_OK;
     }
     Pieces pc;
     if (int rc = make_pieces(h, st, 1 << 30, pc)) return rc;
+    const uint64_t D = pc.D;
+    if (D == 0) {  // nothing deferred: the schedule is wave 0 alone
+        h->flat = true;
+        return ACLZ_OK;
+    }
     Dev &defscan = pc.defscan, &P = pc.P, &owner = pc.owner, &off = pc.off, &dmk = pc.dmk;
     const uint64_t np = pc.np;
     const unsigned long long def_bytes = pc.def_bytes;
@@ -425,6 +434,7 @@ extern "C" int aclz_reshape(aclz_handle *h, uint32_t rounds, void *stream) {
     const uint32_t nb = h->n_blocks;
     Pieces pc;
     if (int rc = make_pieces(h, st, (int)rounds, pc)) return rc;
+    if (pc.D == 0) return ACLZ_OK;
     Dev cnt, tok2, blk2;
     FCK(cudaMalloc(&cnt.p, 4 * (nt + 1)));
     k_rs_count<<<grid_for(nt), 256, 0, st>>>((const uint4 *)h->d_tok, pc.defscan.as<uint32_t>(), pc.off.as<uint64_t>(),

@@ -608,11 +608,13 @@ int aclz::build_index(aclz_handle *h, bool has_tags, uint32_t given_waves, bool 
     DevBuf tags, done;
     CK(cudaMalloc(&tags.p, 4 * (nt ? nt : 1)));
     uint32_t *d_tags = (uint32_t *)tags.p;
+    h->local_tags = false;
     if (has_tags) {
         k_extract_tags<<<1024, 256, 0, st>>>((const uint4 *)h->d_tok, d_tags, nt);
         k_tags_check<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_tokdst,
                                                d_tags, nb, h->log2_bs, nt, d_maxtag, h->d_err);
     } else if (flat_up) {
+        h->local_tags = true;
         k_tags_local<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_tokdst, d_tags, nb,
                                                h->log2_bs, d_maxtag);
         k_store_tags<<<1024, 256, 0, st>>>((uint4 *)h->d_tok, d_tags, nt);
@@ -644,9 +646,12 @@ int aclz::build_index(aclz_handle *h, bool has_tags, uint32_t given_waves, bool 
     h->wave_start.assign(h->n_waves + 1, 0);
     CK(cudaMemsetAsync(h->d_slot, 0xff, 4 * nt, st));
     unsigned long long defb_total = 0;
-    if (maxtag > 0) {
+    // The plain schedule keeps a dense (wave, block) count table and
+    // per-block wave bitmasks, quadratic in the chain depth; beyond 2^28
+    // cells the upload builds the flattened two-wave schedule instead.
+    h->needs_flatten = maxtag > 0 && (uint64_t)maxtag * nb > (1ULL << 28);
+    if (maxtag > 0 && !h->needs_flatten) {
         const uint64_t M = (uint64_t)maxtag * nb;
-        if (M > (1ULL << 31)) { cleanup(); return ACLZ_E_UNSUPPORTED; }
         DevBuf cnt, starts;
         CK(cudaMalloc(&cnt.p, 4 * M));
         CK(cudaMalloc(&starts.p, 8 * (maxtag + 1)));
@@ -765,7 +770,7 @@ extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, 
     }
     rc = build_index(h, (v.flags & kFlagWaves) != 0, v.n_waves, flat_up, stream);
     if (rc) { cleanup(); return rc; }
-    if (flat_up) {
+    if (flat_up || h->needs_flatten) {
         rc = aclz_flatten(h, stream);
         if (rc) { cleanup(); return rc; }
     }
@@ -853,7 +858,7 @@ extern "C" int aclz_set_range_bytes(aclz_handle *h, uint32_t range_bytes, void *
 }
 
 extern "C" int aclz_export(const aclz_handle *h, void *host_out, uint64_t cap, uint64_t *out_size) {
-    if (!h || !out_size || h->flat) return ACLZ_E_INVAL;
+    if (!h || !out_size || h->local_tags) return ACLZ_E_INVAL;
     const uint64_t nt = h->n_tokens, nl = h->n_literals;
     const uint32_t nb = h->n_blocks;
     const uint64_t need = kHdr + (uint64_t)kDirent * nb + (uint64_t)kTok * nt + nl;
@@ -874,7 +879,9 @@ extern "C" int aclz_export(const aclz_handle *h, void *host_out, uint64_t cap, u
         note_cuda_error(e);
         return ACLZ_E_CUDA;
     }
-    const bool tagged = h->n_waves > 0;
+    uint32_t waves = 0;  // the tags' wave count (the schedule may be flattened)
+    for (uint64_t t = 0; t < nt; t++) waves = std::max(waves, (rd32(tok + kTok * t + 12) >> 8) + 1);
+    const bool tagged = nt > 0;
     std::memset(c, 0, kHdr);
     c[0] = 'A'; c[1] = 'C'; c[2] = 'L'; c[3] = 'Z';
     wr16(c + 4, 1);
@@ -884,7 +891,7 @@ extern "C" int aclz_export(const aclz_handle *h, void *host_out, uint64_t cap, u
     wr32(c + 20, nb);
     wr64(c + 24, nt);
     wr64(c + 32, nl);
-    wr32(c + 40, tagged ? h->n_waves : 0);
+    wr32(c + 40, tagged ? waves : 0);
     std::memcpy(c + 44, h->mm, 4);
     const uint32_t bounds[3] = {128, 16384, 2097152};
     for (int i = 0; i < 3; i++) wr32(c + 48 + 4 * i, bounds[i]);

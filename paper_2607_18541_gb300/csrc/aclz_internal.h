@@ -117,5 +117,11 @@ struct aclz_handle {
     // set by aclz_flatten: the deferred work items are origin pieces in one
     // wave, built at flatten time (wave 0 writes no triplets)
     bool flat = false;
+    // set when the (wave, block) tables of the plain schedule would be too
+    // large (deep copy chains): the upload then flattens
+    bool needs_flatten = false;
+    // the stored tags are the 0/1 "in order or not" tags of the flattening
+    // upload, not a legal wave tagging of the container
+    bool local_tags = false;
     uint64_t n_matches_deferred = 0;  // deferred matches before flattening
 };

@@ -398,9 +398,52 @@ def test_export_writes_the_minimal_tags_and_reuploads(kind):
         aclz.aclz_reshape(h, 1, s)
         e2 = aclz.aclz_export(h)
         assert oracle.validate(e2) == 0 and np.array_equal(oracle.decode(e2), exp)
+        # flattening keeps the (minimal) tags, so the stream still exports
         aclz.aclz_flatten(h, s)
+        e3 = aclz.aclz_export(h)
+        assert np.array_equal(e3, e2)
+    finally:
+        aclz.aclz_free(h)
+    # the 0/1 tags of a flattening upload of an untagged container do not
+    h = aclz.aclz_upload(c, s, flags=aclz.ACLZ_UPLOAD_FLATTEN)
+    try:
         with pytest.raises(aclz.AclzError):
             aclz.aclz_export(h)
+    finally:
+        aclz.aclz_free(h)
+
+
+def test_deep_chains_flatten_on_plain_upload():
+    """A chain of copies through every block: block b's match copies block
+    b - 1's match, so minimal tags run 0 .. n_blocks - 1 and the plain
+    schedule's (wave, block) table would pass 2^28 cells; the plain upload
+    then builds the flattened schedule, keeps the minimal tags, and decodes
+    the bytes."""
+    nb, bs = 1 << 17, 64
+    total = nb * bs
+    blk = np.concatenate([[1], np.ones(nb - 1)]).astype(np.uint32)
+    ll = np.full(nb, 48, np.uint32)
+    ml = np.full(nb, 16, np.uint32)
+    src = (np.arange(nb, dtype=np.uint64) - 1) * bs + 48
+    ll[0], ml[0], src[0] = 64, 0, 0
+    lits = np.random.default_rng(46).integers(0, 256, int(ll.sum()), dtype=np.uint8)
+    c = aclz.aclz_pack(total, bs, (4, 4, 4, 4), blk, ll, ml, src, lits)
+    exp = oracle.decode(c)
+    mt, nw = oracle.min_tags(c)
+    assert nw == nb and (nw - 1) * nb > (1 << 28)
+    s = torch.cuda.current_stream()
+    h = aclz.aclz_upload(c, s)
+    try:
+        assert aclz.aclz_handle_info(h).n_waves == 2
+        assert np.array_equal(aclz.aclz_tags(h), mt)
+        out = torch.empty(total + 16, dtype=torch.uint8, device="cuda")
+        for mode, flags in MODES:
+            out.zero_()
+            aclz.aclz_decode_all(h, out, mode=mode, flags=flags, stream=s)
+            assert aclz.aclz_device_status(h, s) == 0
+            assert np.array_equal(out[:total].cpu().numpy(), exp), (mode, flags)
+        e = aclz.aclz_export(h)
+        assert oracle.header(e).n_waves == nw and np.array_equal(oracle.tokens(e)[4], mt)
     finally:
         aclz.aclz_free(h)
 
