@@ -39,6 +39,9 @@ constexpr int kUnrollCopy = 4;   // chunks per lane per round in match copies
 constexpr uint32_t kTmaMin = 192;
 constexpr uint32_t kPiece = 2048;
 constexpr uint32_t kSmemPerSm = 220u * 1024u;  // stage memory shared by the CTAs of one SM
+// waves with fewer triplets than about 152 SMs x 16 groups x 64 go one
+// window per group
+constexpr uint64_t kSmallWave = 155648;
 
 __device__ __forceinline__ uint64_t tri_dst(const uint4 t) { return (uint64_t)t.x | ((uint64_t)(t.y & 0xffu) << 32); }
 __device__ __forceinline__ uint64_t tri_src(const uint4 t) { return (uint64_t)t.z | ((uint64_t)(t.w & 0xffu) << 32); }
@@ -328,9 +331,16 @@ int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st, cudaEvent_t phas
     for (uint32_t w = 1; w < h->n_waves; w++) {
         const uint64_t a = h->wave_start[w], n = h->wave_start[w + 1] - a;
         if (!n) continue;
-        const uint64_t groups = (n + (uint64_t)G * ITEMS - 1) / ((uint64_t)G * ITEMS);
+        // small waves: one window of G triplets per group, so more groups
+        // share the wave (about one full round of the GPU's resident groups)
+        const bool small = n < kSmallWave;
+        const uint64_t per = (uint64_t)G * (small ? 1 : ITEMS);
+        const uint64_t groups = (n + per - 1) / per;
         const unsigned grid = (unsigned)((groups + gpc - 1) / gpc);
-        k_wave_copy<G, ITEMS><<<grid, kThreads, 0, st>>>((const uint4 *)h->d_tri + a, n, out, h->log2_bs);
+        if (small)
+            k_wave_copy<G, 1><<<grid, kThreads, 0, st>>>((const uint4 *)h->d_tri + a, n, out, h->log2_bs);
+        else
+            k_wave_copy<G, ITEMS><<<grid, kThreads, 0, st>>>((const uint4 *)h->d_tri + a, n, out, h->log2_bs);
     }
     return cudaGetLastError() == cudaSuccess ? ACLZ_OK : ACLZ_E_CUDA;
 }
