@@ -61,6 +61,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x over the ranks of the process group (x itself alone)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(ms_max: float, bytes_per_rank: int, world: int) -> float:
+    """Whole-job output GB/s of `world` independent replicas, each decoding
+    bytes_per_rank per step, timed by the slowest rank."""
+    return world * bytes_per_rank / (ms_max * 1e-3) / 1e9
+
+
 def make_workload(total, bs, L, seed_offset=0):
     from paper_2607_18541_gb300 import synth
     return synth.copy_sweep(total, bs, L, seed=synth.SEED_COPY + L + seed_offset)
@@ -319,11 +336,8 @@ def run_ours(args):
     ms_w0 = [s_.elapsed_time(m) for s_, m in zip(starts, mids)]
     ms_def = [m.elapsed_time(e) for m, e in zip(mids, ends)]
     ms_step = sum(ms) / len(ms)
-    t = torch.tensor([ms_step], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * sw.total / (ms_max * 1e-3) / 1e9
+    ms_max = max_over_ranks(ms_step, dev)
+    value = replica_value(ms_max, sw.total, world)
     peak, peak_kind = peaks()
     w0_ms, d_ms = statistics.mean(ms_w0), statistics.mean(ms_def)
     if d_ms >= w0_ms and n_def:
@@ -356,7 +370,7 @@ def run_ours(args):
             aclz.aclz_free(hh)
             if i:
                 e2e_ms.append(dt * 1e3)
-    e2e_val = world * sw.total / (statistics.mean(e2e_ms) * 1e-3) / 1e9
+    e2e_val = replica_value(max_over_ranks(statistics.mean(e2e_ms), dev), sw.total, world)
     if rank == 0:
         line = {
             "metric": f"match-phase decode output GB/s (copy sweep, L={args.L})",

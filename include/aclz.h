@@ -332,6 +332,14 @@ int aclz_block_features(const void *d_x, uint64_t n, uint32_t block_size, float 
  * calls on h since the last call (ACLZ_OK, ACLZ_E_TIMEOUT, ACLZ_E_DEVICE). */
 int aclz_device_status(aclz_handle *h, void *stream);
 
+/* Failure-detection self-test (no counterpart in the paper): one group waits
+ * on a completion word that nothing sets, with the bounded wait the
+ * persistent decode uses on its source blocks, for at most spin_limit polls
+ * (1 .. 2^22).  Returns ACLZ_E_TIMEOUT, the expected outcome: the wait gave
+ * up, set the error word and the kernel returned, leaving the context
+ * usable.  ACLZ_OK would mean the wait did not time out.  Synchronizes. */
+int aclz_selftest_wait(uint32_t spin_limit, void *stream);
+
 /* FNV-1a 64 of each 64 KiB chunk of d_buf, then FNV-1a 64 of the chunk
  * hashes (8 LE bytes each) followed by n (8 LE bytes).  Synchronous:
  * *out_hash holds the result on return.  Allocates stream-ordered scratch

@@ -87,6 +87,7 @@ _SIGS = [
     ("aclz_tags", _I, [_VP, _U32P, _U64]),
     ("aclz_set_range_bytes", _I, [_VP, _U32, _VP]),
     ("aclz_flatten", _I, [_VP, _VP]),
+    ("aclz_selftest_wait", _I, [_U32, _VP]),
     ("aclz_export", _I, [_VP, _VP, _U64, _U64P]),
     ("aclz_reshape", _I, [_VP, _U32, _VP]),
     ("aclz_decode_all", _I, [_VP, _VP, _U64, ctypes.POINTER(aclz_decode_cfg), _VP]),
@@ -270,6 +271,11 @@ def aclz_export(h: int) -> np.ndarray:
     out = np.empty(size.value, dtype=np.uint8)
     _ck(lib().aclz_export(h, _hptr(out), out.size, ctypes.byref(size)), "aclz_export")
     return out
+
+
+def aclz_selftest_wait(spin_limit: int, stream=None) -> int:
+    """Status of the bounded-wait self-test (ACLZ_E_TIMEOUT expected)."""
+    return int(lib().aclz_selftest_wait(spin_limit, _stream(stream)))
 
 
 def aclz_flatten(h: int, stream=None) -> None:

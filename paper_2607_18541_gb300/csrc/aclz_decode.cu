@@ -528,6 +528,40 @@ extern "C" int aclz_decode_all(aclz_handle *h, void *d_out, uint64_t cap, const 
     return aclz_decode_all_ev(h, d_out, cap, cfg, stream, nullptr);
 }
 
+namespace {
+
+// One group waits, bounded, for wave bit 0 of a block whose bits nothing
+// sets: the wait the persistent decode does on a stuck source.
+__global__ void k_wait_selftest(const unsigned long long *done, uint32_t spin_limit, uint32_t *err) {
+    wait_waves_below(done, 1u, err, spin_limit);
+}
+
+}  // namespace
+
+extern "C" int aclz_selftest_wait(uint32_t spin_limit, void *stream) {
+    if (spin_limit == 0 || spin_limit > kSpinLimitMin) return ACLZ_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *buf = nullptr;
+    if (cudaError_t e = cudaMalloc(&buf, 64); e != cudaSuccess) {
+        note_cuda_error(e);
+        return ACLZ_E_NOMEM;
+    }
+    uint32_t err = 0;
+    cudaError_t e = cudaMemsetAsync(buf, 0, 64, st);
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32, 0, st>>>((const unsigned long long *)buf, spin_limit, (uint32_t *)buf + 8);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, (uint32_t *)buf + 8, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        return ACLZ_E_CUDA;
+    }
+    return (err & kErrTimeout) ? ACLZ_E_TIMEOUT : ACLZ_OK;
+}
+
 extern "C" int aclz_device_status(aclz_handle *h, void *stream) {
     if (!h) return ACLZ_E_INVAL;
     uint32_t e = 0;

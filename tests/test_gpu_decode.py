@@ -520,3 +520,17 @@ def test_copy_sweep_1gib_full_size(L):
     got, f, info = gpu_decode(c, 32, (aclz.ACLZ_MODE_AUTO, 0), range_bytes=8192, ctas_per_sm=2, phase_event=ev)
     assert np.array_equal(got, exp)
     assert f == fe
+
+
+# ------------------------------------------------------ failure detection
+
+def test_bounded_wait_times_out_and_the_context_stays_usable():
+    """A wait on a completion word that nothing sets gives up after its poll
+    limit, reports ACLZ_E_TIMEOUT, and the GPU keeps working (a decode right
+    after is exact)."""
+    s = torch.cuda.current_stream()
+    assert aclz.aclz_selftest_wait(2000, s) == aclz.ACLZ_E_TIMEOUT
+    assert aclz.aclz_selftest_wait(0, s) == aclz.ACLZ_E_INVAL
+    c = _flatten_case("markov_base")
+    got, f, info = gpu_decode(c, 32, PERSIST_STAGED)
+    assert np.array_equal(got, oracle.decode(c))
