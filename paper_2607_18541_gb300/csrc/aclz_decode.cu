@@ -95,12 +95,19 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
     const uint64_t t0 = blk_tok[b], t1 = blk_tok[b + 1];
     uint64_t lbase = blk_lit[b];
     uint64_t pos = (uint64_t)b << log2bs;
+    // the next window's tokens and worklist slots are loaded while the
+    // current window is copied
     uint4 nt = t0 + g.lane < t1 ? __ldg(tok + t0 + g.lane) : make_uint4(0, 0, 0, 0);
+    uint32_t ns = (tri && t0 + g.lane < t1) ? __ldg(slot + t0 + g.lane) : 0u;
     for (uint64_t w = t0; w < t1; w += G) {
         const uint64_t i = w + g.lane;
         const bool v = i < t1;
         const uint4 t = v ? nt : make_uint4(0, 0, 0, 0);
-        if (w + G + g.lane < t1) nt = __ldg(tok + w + G + g.lane);
+        const uint32_t sl = ns;
+        if (w + G + g.lane < t1) {
+            nt = __ldg(tok + w + G + g.lane);
+            if (tri) ns = __ldg(slot + w + G + g.lane);
+        }
         const uint32_t ll = t.x, ml = t.y;
         const uint32_t tag = t.w >> 8;
         const uint64_t src = (uint64_t)t.z | ((uint64_t)(t.w & 0xffu) << 32);
@@ -110,7 +117,6 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
         const uint64_t dm = dl + ll;
         // deferred matches go to their wave's worklist
         if (tri && v && ml && tag) {
-            const uint32_t sl = __ldg(slot + i);
             __stcg(tri + sl, make_uint4((uint32_t)dm, (uint32_t)(dm >> 32), (uint32_t)src,
                                         (uint32_t)(src >> 32) | (ml << 8)));
         }
