@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, STAGED ? 1 : 3)
 // that start in [k*T, (k+1)*T); a segment crossing the range end is
 // finished by the group that started it.
 template <int G, int ITEMS>
-__global__ void __launch_bounds__(kThreads) k_wave_copy(const uint4 *__restrict__ tri, uint64_t n,
+__global__ void __launch_bounds__(kThreads, 3) k_wave_copy(const uint4 *__restrict__ tri, uint64_t n,
                                                         uint8_t *out, uint32_t log2bs) {
     Group<G> g;
     constexpr uint64_t T = (uint64_t)G * ITEMS;
