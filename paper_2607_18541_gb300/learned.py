@@ -303,7 +303,7 @@ class Model:
 
 def encode_learned(model: Model, x, block_size: int = BLOCK, tau: float = 0.0, passes: int = 6,
                    base=None, fb=None):
-    """Per-block thresholds from the network, judged by the plain encoder's
+    """Per-block thresholds from the network, checked against the plain encoder's
     ratio and decode speed: the result is kept only if its estimated size
     and its token count (the decode-speed lever, Sec. III-C) are both no
     larger than the fixed 12/16/24/32 encode's.  When one is larger, the
@@ -396,7 +396,7 @@ def train_default(scale: int = 1, steps: int = 2000, seed: int = 20260712, log=p
 
 class Choices:
     """Known per-block choices in the place of the network (the label bound
-    of a stream: its own Lagrangian labels, through the same judge)."""
+    of a stream: its own Lagrangian labels, through the same check)."""
 
     def __init__(self, k):
         self.k = np.asarray(k)

@@ -114,7 +114,7 @@ def test_training_lowers_loss_and_learned_encode_is_exact():
     c, k = learned.encode_learned(model, x)
     assert np.array_equal(oracle.decode(c), x)
     fb = learned.encode(x, learned.CANDIDATES[learned.FALLBACK])
-    # the judge: no larger estimated size and no more tokens than 12/16/24/32
+    # the size-and-token check: no larger estimated size and no more tokens than 12/16/24/32
     assert learned.est_bytes(c) <= learned.est_bytes(fb)
     assert learned.read_tokens(c)[0].sum() <= learned.read_tokens(fb)[0].sum()
     h = aclz.aclz_upload(c, torch.cuda.current_stream())

@@ -147,7 +147,7 @@ class _FixedChoices:
 
 
 @pytest.mark.parametrize("kind", ["lagrange", "all_push", "all_base"])
-def test_judge_never_returns_a_larger_or_slower_encode(monkeypatch, mixed, kind):
+def test_check_never_returns_a_larger_or_slower_encode(monkeypatch, mixed, kind):
     bs = 1 << 14
     nb = -(-mixed.size // bs)
     monkeypatch.setattr(learned, "features", lambda x, base, block_size=bs: np.zeros((nb, learned.N_FEATURES)))
