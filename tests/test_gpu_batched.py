@@ -94,3 +94,21 @@ def test_autotune_on_a_merged_batch_and_decode_with_its_choice():
             assert np.array_equal(dec.stream_output(i).cpu().numpy(), x), i
     finally:
         dec.close()
+
+
+def test_flattened_batch_decodes_every_stream():
+    streams = batched.make_streams(32, 16 << 10, 1 << 20, seed=321)
+    p = aclz.aclz_encode_params_default(aclz.ACLZ_PRESET_BASE)
+    p.block_size = 1 << 12
+    cs = batched.encode_streams(streams, p)
+    s = torch.cuda.current_stream()
+    dec = batched.BatchDecoder(cs, stream=s, flatten=True)
+    try:
+        assert aclz.aclz_handle_info(dec.h).n_waves <= 2
+        dec.capture()
+        dec.replay()
+        assert aclz.aclz_device_status(dec.h, s) == 0
+        for i, x in enumerate(streams):
+            assert np.array_equal(dec.stream_output(i).cpu().numpy(), x), i
+    finally:
+        dec.close()
