@@ -328,3 +328,28 @@ def test_markov_repeat_rate_and_copy_sweep_recipe():
     assert x.min() >= 0x30 and x.max() <= 0x6F
     # same seed, same bytes
     assert np.array_equal(x, synth.markov2(1 << 20, seed=1))
+
+
+def test_stats_count_a_hand_built_parse():
+    # one block holding matches at distances in every band (Sec. IV-B:
+    # < 128, < 16384, < 2097152, >= 2097152) and of lengths 8 .. 100
+    total = 3 << 20
+    # (literal run, match length, distance)
+    plan = [(2200000, 8, 100), (10, 20, 127), (3, 40, 128), (0, 8, 16383), (5, 100, 16384),
+            (0, 20, 2097151), (0, 12, 2097152)]
+    pos, toks = 0, []
+    for ll, ml, dist in plan:
+        pos += ll
+        toks.append((ll, ml, pos - dist))
+        pos += ml
+    toks.append((total - pos, 0, 0))
+    nlit = sum(t[0] for t in toks)
+    lits = np.random.default_rng(8).integers(0, 256, nlit, dtype=np.uint8)
+    c = oracle.pack(total, 4 << 20, [len(toks)], [t[0] for t in toks], [t[1] for t in toks],
+                    [t[2] for t in toks], lits, tags=False)
+    st = oracle.stats(c)
+    assert st.matches == 7 and st.match_bytes == 8 + 20 + 40 + 8 + 100 + 20 + 12
+    assert st.literal_bytes == nlit and st.literal_bytes + st.match_bytes == total
+    assert st.lt16 == 3 and st.lt32 == 5
+    assert st.per_class == (2, 2, 2, 1)
+    assert st.tokens == 8 and st.blocks == 1 and st.total_len == total
