@@ -24,6 +24,7 @@
 // shared memory by TMA bulk copies (cp.async.bulk + mbarrier).
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "aclz_device.cuh"
 #include "aclz_internal.h"
@@ -384,6 +385,10 @@ int launch_persistent(aclz_handle *h, uint8_t *out, uint32_t ctas_per_sm, cudaSt
     auto fn = k_ranges<G, STAGED>;
     static int sms = 0;
     static Occ occ[5][33];  // [ctas_per_sm request 0..4][G]
+    // the occupancy cache and the kernel's shared-memory attribute are
+    // process-wide: host threads take turns from the lookup to the launch
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     const uint32_t req = std::min<uint32_t>(ctas_per_sm, 4);
     Occ &o = occ[req][G];
     if (!o.per_sm) {

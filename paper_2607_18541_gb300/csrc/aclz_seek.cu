@@ -164,16 +164,16 @@ __global__ void __launch_bounds__(kSeekThreads) k_seek(const SeekReq *__restrict
 int seek_launch(aclz_handle *h, const SeekReq *d_reqs, const SeekReq &one, uint32_t nreq, uint64_t nseg,
                 cudaStream_t st) {
     if (!nseg) return ACLZ_OK;
-    static int sms = 0, per_sm = 0;
-    if (!sms) {
-        int dev = 0;
+    // SM count and resident CTAs, found once (thread-safe static init)
+    static const uint64_t slots = [] {
+        int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seek, kSeekThreads, 0);
-        if (per_sm < 1) per_sm = 1;
-    }
+        return (uint64_t)std::max(sms, 1) * (uint64_t)std::max(per_sm, 1);
+    }();
     const uint64_t need = (nseg + kSeekWarps - 1) / kSeekWarps;
-    const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sms * per_sm, need);
+    const unsigned grid = (unsigned)std::min<uint64_t>(slots, need);
     SeekIndex ix;
     ix.tok = (const uint4 *)h->d_tok;
     ix.lit = h->d_lit;
