@@ -198,7 +198,7 @@ int aclz_reshape(aclz_handle *h, uint32_t rounds, void *stream);
 
 /* Regroup the persistent schedule: consecutive (block, wave) segments are
  * packed into work ranges of about range_bytes of deferred matches (upload
- * picks 16 KiB).  Synchronizes the stream.  Used by the autotuner. */
+ * picks 4 KiB).  Synchronizes the stream.  Used by the autotuner. */
 int aclz_set_range_bytes(aclz_handle *h, uint32_t range_bytes, void *stream);
 
 typedef struct aclz_decode_cfg {

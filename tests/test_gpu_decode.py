@@ -514,10 +514,10 @@ def test_copy_sweep_1gib_full_size(L):
         got, f, info = gpu_decode(c, 32, mode)
         assert np.array_equal(got, exp)
         assert f == fe
-    # the benchmark's exact launch: AUTO, 2 CTAs per SM, 8 KiB ranges, phase event
+    # the benchmark's exact launch: AUTO, 2 CTAs per SM, 4 KiB ranges, phase event
     ev = torch.cuda.Event(enable_timing=True)
     ev.record()
-    got, f, info = gpu_decode(c, 32, (aclz.ACLZ_MODE_AUTO, 0), range_bytes=8192, ctas_per_sm=2, phase_event=ev)
+    got, f, info = gpu_decode(c, 32, (aclz.ACLZ_MODE_AUTO, 0), range_bytes=4096, ctas_per_sm=2, phase_event=ev)
     assert np.array_equal(got, exp)
     assert f == fe
 
