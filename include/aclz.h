@@ -141,6 +141,7 @@ int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_handle **ou
  * plain schedule would need more than 2^28 (wave, block) cells (copy chains
  * thousands of waves deep) also flattens. */
 #define ACLZ_UPLOAD_FLATTEN 1u
+
 int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out);
 
 /* Write the handle's stream back as a host container, with the wave tags
@@ -157,6 +158,10 @@ int aclz_export(const aclz_handle *h, void *host_out, uint64_t cap, uint64_t *ou
 /* Free a handle and its device memory (after its work has completed). */
 int aclz_free(aclz_handle *h);
 
+/* Sizes of the uploaded stream and of its decode schedule: total_len,
+ * n_tokens, n_literals, block_size, n_blocks, min_match as in the
+ * container; n_waves and n_deferred (work items of waves >= 1) as the
+ * schedule stands (after aclz_flatten: 2 and the number of pieces). */
 int aclz_handle_info(const aclz_handle *h, aclz_info *out);
 
 /* Per-wave deferred-match counts (wave 0 holds literals and in-order
@@ -288,11 +293,17 @@ int aclz_batch_merge(uint32_t n, const void *const *host_bufs, const uint64_t *s
 
 /* CUDA graph of one aclz_decode_all(h, d_out, cap, cfg) call, captured on
  * a private stream after one plain decode on `stream` (which it
- * synchronizes).  Launching the graph repeats the whole decode. */
+ * synchronizes).  Launching the graph repeats the whole decode.  Errors as
+ * aclz_decode_all; *out is owned by the caller (aclz_graph_free). */
 typedef struct aclz_graph aclz_graph;
 int aclz_graph_create(aclz_handle *h, void *d_out, uint64_t cap, const aclz_decode_cfg *cfg, void *stream,
                       aclz_graph **out);
+
+/* Enqueue the captured decode on `stream` (asynchronous; the handle, the
+ * output buffer and the graph must stay alive until it completes). */
 int aclz_graph_launch(aclz_graph *g, void *stream);
+
+/* Destroy a graph (after its launches have completed). */
 int aclz_graph_free(aclz_graph *g);
 
 /* ---- learned per-block thresholds (no counterpart in the paper's
