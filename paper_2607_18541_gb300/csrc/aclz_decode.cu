@@ -43,6 +43,9 @@ constexpr uint32_t kSmemPerSm = 220u * 1024u;  // stage memory shared by the CTA
 // waves with fewer triplets than about 152 SMs x 16 groups x 64 go one
 // window per group
 constexpr uint64_t kSmallWave = 155648;
+// per-wave copies put full chunks first when deferred matches average
+// at least this many bytes
+constexpr double kFullFirstMin = 48.0;
 
 __device__ __forceinline__ uint64_t tri_dst(const uint4 t) { return (uint64_t)t.x | ((uint64_t)(t.y & 0xffu) << 32); }
 __device__ __forceinline__ uint64_t tri_src(const uint4 t) { return (uint64_t)t.z | ((uint64_t)(t.w & 0xffu) << 32); }
@@ -269,8 +272,10 @@ __global__ void __launch_bounds__(kThreads, STAGED ? 1 : 3)
 
 // Copy one wave's worklist.  Group k owns the segments (runs of one block)
 // that start in [k*T, (k+1)*T); a segment crossing the range end is
-// finished by the group that started it.
-template <int G, int ITEMS>
+// finished by the group that started it.  FULL_FIRST: the matches' full
+// 16-byte chunks are copied before their partial ones (for matches of
+// several chunks); otherwise chunks go in match order.
+template <int G, int ITEMS, bool FULL_FIRST>
 __global__ void __launch_bounds__(kThreads, 3) k_wave_copy(const uint4 *__restrict__ tri, uint64_t n,
                                                         uint8_t *out, uint32_t log2bs) {
     Group<G> g;
@@ -318,7 +323,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_wave_copy(const uint4 *__restri
             const unsigned lim = dmask & (0u - dmask);
             const unsigned batch = lim ? (rem & (lim - 1u)) : rem;
             const bool mine = (batch >> g.lane) & 1u;
-            group_copy<G, kUnrollCopy>(g, out, d, out + sr, mine ? len : 0u);
+            if (FULL_FIRST)
+                group_copy_full_first<G, kUnrollCopy>(g, out, d, out + sr, mine ? len : 0u);
+            else
+                group_copy<G, kUnrollCopy>(g, out, d, out + sr, mine ? len : 0u);
             g.sync();
             rem &= ~batch;
         }
@@ -335,6 +343,9 @@ int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st, cudaEvent_t phas
                                             h->n_blocks, h->log2_bs, nullptr, nullptr, 0);
     if (phase) cudaEventRecord(phase, st);
     constexpr int ITEMS = 2;
+    // deferred matches of three or more 16-byte chunks on average: full
+    // chunks first
+    const bool ff = h->mean_deferred_len >= (double)kFullFirstMin;
     for (uint32_t w = 1; w < h->n_waves; w++) {
         const uint64_t a = h->wave_start[w], n = h->wave_start[w + 1] - a;
         if (!n) continue;
@@ -344,10 +355,15 @@ int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st, cudaEvent_t phas
         const uint64_t per = (uint64_t)G * (small ? 1 : ITEMS);
         const uint64_t groups = (n + per - 1) / per;
         const unsigned grid = (unsigned)((groups + gpc - 1) / gpc);
-        if (small)
-            k_wave_copy<G, 1><<<grid, kThreads, 0, st>>>((const uint4 *)h->d_tri + a, n, out, h->log2_bs);
+        const uint4 *t = (const uint4 *)h->d_tri + a;
+        if (small && ff)
+            k_wave_copy<G, 1, true><<<grid, kThreads, 0, st>>>(t, n, out, h->log2_bs);
+        else if (small)
+            k_wave_copy<G, 1, false><<<grid, kThreads, 0, st>>>(t, n, out, h->log2_bs);
+        else if (ff)
+            k_wave_copy<G, ITEMS, true><<<grid, kThreads, 0, st>>>(t, n, out, h->log2_bs);
         else
-            k_wave_copy<G, ITEMS><<<grid, kThreads, 0, st>>>((const uint4 *)h->d_tri + a, n, out, h->log2_bs);
+            k_wave_copy<G, ITEMS, false><<<grid, kThreads, 0, st>>>(t, n, out, h->log2_bs);
     }
     return cudaGetLastError() == cudaSuccess ? ACLZ_OK : ACLZ_E_CUDA;
 }

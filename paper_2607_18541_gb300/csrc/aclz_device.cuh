@@ -138,17 +138,27 @@ __device__ __forceinline__ void chunk_store(uint8_t *dst, uint32_t lo, uint32_t 
         store_partial16(dst, v, lo, hi);
 }
 
-// Packed group copy.  Each lane holds one job (d: output offset, s: source
-// pointer, n: length; n == 0 for none).  The jobs' output chunks are
-// numbered in lane order and dealt to the group's lanes, U per lane per
-// round, loads issued before stores.  Jobs must be independent: no job's
-// source may overlap another job's output in the same call.
-template <int G, int U, bool SMEM = false>
-__device__ __forceinline__ void group_copy(const Group<G> &g, uint8_t *out, uint64_t d,
-                                           const uint8_t *s, uint32_t n) {
-    const uint32_t c = n ? (uint32_t)(((d + n - 1) >> 4) - (d >> 4) + 1) : 0u;
-    const uint32_t incl = g.scan_incl(c);
-    const uint32_t total = g.shfl(incl, G - 1);
+// Lane of the group's first job whose inclusive prefix count exceeds k.
+template <int G>
+__device__ __forceinline__ int owner_lane(const Group<G> &g, uint32_t incl, uint32_t k) {
+    int lo = 0, hi = G - 1;
+#pragma unroll
+    for (int st = G; st > 1; st >>= 1) {
+        const int mid = (lo + hi) >> 1;
+        const uint32_t v = g.shfl(incl, mid);
+        if (v > k) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Packed group copy, chunks in job order: the jobs' aligned 16-byte output
+// chunks (c per lane, inclusive prefix incl, total in all) are numbered in
+// lane order and dealt to the group's lanes, U per lane per round, loads
+// issued before stores.
+template <int G, int U, bool SMEM>
+__device__ __forceinline__ void copy_chunks_in_order(const Group<G> &g, uint8_t *out, uint64_t d,
+                                                     const uint8_t *s, uint32_t n, uint32_t c,
+                                                     uint32_t incl, uint32_t total) {
     for (uint32_t base = 0; base < total; base += (uint32_t)G * U) {
         uint8_t *dst[U];
         uint32_t lohi[U];
@@ -156,17 +166,12 @@ __device__ __forceinline__ void group_copy(const Group<G> &g, uint8_t *out, uint
         uint32_t r[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            const uint32_t k = base + (uint32_t)u * G + (uint32_t)g.lane;
-            // owner: first lane j with incl_j > k
-            int lo = 0, hi = G - 1;
-#pragma unroll
-            for (int st = G; st > 1; st >>= 1) {
-                const int mid = (lo + hi) >> 1;
-                const uint32_t v = g.shfl(incl, mid);
-                if (v > k) hi = mid; else lo = mid + 1;
-            }
-            const int j = lo;
-            const uint32_t ej = g.shfl(incl, j) - g.shfl(c, j);
+            lohi[u] = 0u;
+            const uint32_t k0 = base + (uint32_t)u * G;  // the same on every lane
+            if (k0 >= total) continue;
+            const uint32_t k = k0 + (uint32_t)g.lane;
+            const int j = owner_lane<G>(g, incl, k);
+            const uint32_t ej = g.shfl(incl - c, j);
             const uint64_t dj = g.shfl(d, j);
             const uint8_t *sj = reinterpret_cast<const uint8_t *>(
                 g.shfl(reinterpret_cast<unsigned long long>(s), j));
@@ -176,13 +181,113 @@ __device__ __forceinline__ void group_copy(const Group<G> &g, uint8_t *out, uint
             const uint64_t bhi = (dj + nj) < (A + 16) ? (dj + nj) : (A + 16);
             const uint32_t clo = (uint32_t)(blo - A), chi = (uint32_t)(bhi - A);
             dst[u] = out + A;
-            lohi[u] = k < total ? (clo | (chi << 8)) : 0u;
-            if (k < total) chunk_load<SMEM>(sj + (blo - dj), clo, chi, a[u], b[u], r[u]);
+            if (k < total) {
+                lohi[u] = clo | (chi << 8);
+                chunk_load<SMEM>(sj + (blo - dj), clo, chi, a[u], b[u], r[u]);
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; u++)
             if (lohi[u]) chunk_store(dst[u], lohi[u] & 0xff, lohi[u] >> 8, a[u], b[u], r[u]);
     }
+}
+
+// Packed group copy, full chunks first: every job's full 16-byte chunks
+// (in lane order), then the partial head and tail chunks, dealt as above.
+// A slot of G chunks is then all full 16-byte stores or all narrow partial
+// stores, except the one slot at the boundary, so the narrow-store path
+// runs once per G partial chunks instead of in every slot.
+template <int G, int U, bool SMEM>
+__device__ __forceinline__ void copy_chunks_full_first(const Group<G> &g, uint8_t *out, uint64_t d,
+                                                       const uint8_t *s, uint32_t n, uint32_t c) {
+    const uint64_t e = d + n;
+    // chunk 0 is partial unless it starts at d and is filled; the last
+    // chunk (if another) is partial unless the job ends on a boundary
+    const uint32_t p0 = (n && ((d & 15) || (c == 1 && (e & 15)))) ? 1u : 0u;
+    const uint32_t np = p0 + ((c >= 2 && (e & 15)) ? 1u : 0u);
+    const uint32_t nf = c - np;
+    const uint32_t inclF = g.scan_incl(nf);
+    const uint32_t inclP = g.scan_incl(np);
+    const uint32_t exF = inclF - nf, exP = inclP - np;
+    const uint32_t cf = c | (p0 << 31);  // c < 2^21 (jobs are shorter than 2^25 bytes)
+    const uint32_t F = g.shfl(inclF, G - 1);
+    const uint32_t total = F + g.shfl(inclP, G - 1);
+    for (uint32_t base = 0; base < total; base += (uint32_t)G * U) {
+        uint8_t *dst[U];
+        uint32_t lohi[U];
+        uint4 a[U], b[U];
+        uint32_t r[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            lohi[u] = 0u;
+            const uint32_t k0 = base + (uint32_t)u * G;  // the same on every lane
+            if (k0 >= total) continue;
+            const uint32_t k = k0 + (uint32_t)g.lane;
+            const bool full = k < F;
+            // owner among the full chunks, the partial ones, or both (only
+            // in the slot that straddles the boundary); branches are uniform
+            int j;
+            uint32_t exj;
+            if (k0 + G <= F) {
+                j = owner_lane<G>(g, inclF, k);
+                exj = g.shfl(exF, j);
+            } else if (k0 >= F) {
+                j = owner_lane<G>(g, inclP, k - F);
+                exj = g.shfl(exP, j);
+            } else {
+                const int jf = owner_lane<G>(g, inclF, k);
+                const int jp = owner_lane<G>(g, inclP, k - F);
+                j = full ? jf : jp;
+                const uint32_t xf = g.shfl(exF, j), xp = g.shfl(exP, j);
+                exj = full ? xf : xp;
+            }
+            const uint64_t dj = g.shfl(d, j);
+            const uint8_t *sj = reinterpret_cast<const uint8_t *>(
+                g.shfl(reinterpret_cast<unsigned long long>(s), j));
+            const uint32_t nj = g.shfl(n, j);
+            const uint32_t cfj = g.shfl(cf, j);
+            const uint32_t cj = cfj & 0x7fffffffu, p0j = cfj >> 31;
+            // chunk index within the job: full chunks are [p0j, p0j + nf);
+            // the partial ones are chunk 0 (if p0j) then chunk cj - 1
+            const uint32_t idx = full ? p0j + (k - exj) : ((k - F == exj && p0j) ? 0u : cj - 1u);
+            const uint64_t A = ((dj >> 4) + idx) << 4;
+            const uint64_t blo = dj > A ? dj : A;
+            const uint64_t bhi = (dj + nj) < (A + 16) ? (dj + nj) : (A + 16);
+            const uint32_t clo = (uint32_t)(blo - A), chi = (uint32_t)(bhi - A);
+            dst[u] = out + A;
+            if (k < total) {
+                lohi[u] = clo | (chi << 8);
+                chunk_load<SMEM>(sj + (blo - dj), clo, chi, a[u], b[u], r[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (lohi[u]) chunk_store(dst[u], lohi[u] & 0xff, lohi[u] >> 8, a[u], b[u], r[u]);
+    }
+}
+
+// Packed group copies.  Each lane holds one job (d: output offset, s:
+// source pointer, n: length; n == 0 for none), cut into aligned 16-byte
+// output chunks.  group_copy deals the chunks in job order and suits short
+// jobs (literal runs, in-block matches of wave 0); group_copy_full_first
+// deals every job's full chunks first, for match copies of a few chunks or
+// more.  Jobs must be independent: no job's source may overlap another
+// job's output in the same call.
+template <int G, int U, bool SMEM = false>
+__device__ __forceinline__ void group_copy(const Group<G> &g, uint8_t *out, uint64_t d,
+                                           const uint8_t *s, uint32_t n) {
+    const uint32_t c = n ? (uint32_t)(((d + n - 1) >> 4) - (d >> 4) + 1) : 0u;
+    const uint32_t incl = g.scan_incl(c);
+    const uint32_t total = g.shfl(incl, G - 1);
+    copy_chunks_in_order<G, U, SMEM>(g, out, d, s, n, c, incl, total);
+}
+
+template <int G, int U, bool SMEM = false>
+__device__ __forceinline__ void group_copy_full_first(const Group<G> &g, uint8_t *out, uint64_t d,
+                                                      const uint8_t *s, uint32_t n) {
+    const uint32_t c = n ? (uint32_t)(((d + n - 1) >> 4) - (d >> 4) + 1) : 0u;
+    if (!g.ballot(n > 0)) return;
+    copy_chunks_full_first<G, U, SMEM>(g, out, d, s, n, c);
 }
 
 // Bytes [r, r + 16) of a || b for a shift r that is the same on every lane
