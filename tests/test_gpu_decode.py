@@ -216,6 +216,44 @@ def test_misaligned_sources_and_in_block_chains():
         check(c, G)
 
 
+def test_mixed_length_matches_long_on_average():
+    # deferred matches of 1..400 bytes averaging well over three 16-byte
+    # chunks, at every alignment, some one chunk or less, sources near
+    # (in-block chains) and anywhere earlier: the per-wave copies deal full
+    # chunks first here, with jobs of very different chunk counts per window
+    rng = np.random.default_rng(17)
+    blk, ll, ml, sr, lits = [], [], [], [], bytearray()
+    total, bs = 0, 1 << 12
+    for b in range(256):
+        pos, cnt = b * bs, 0
+        end = pos + bs
+        while pos < end:
+            lit = int(rng.integers(0, 12))
+            u = rng.random()
+            m = int(rng.integers(1, 17)) if u < 0.25 else int(rng.integers(17, 65)) if u < 0.5 \
+                else int(rng.integers(65, 401))
+            if pos + lit + m <= end and pos + lit >= m:
+                lo = 0 if rng.random() < 0.5 else max(0, pos + lit - 2000)
+                src = int(rng.integers(lo, pos + lit - m + 1))
+                ll.append(lit); ml.append(m); sr.append(src)
+                lits += rng.bytes(lit)
+                pos += lit + m
+            else:
+                ll.append(end - pos); ml.append(0); sr.append(0)
+                lits += rng.bytes(end - pos)
+                pos = end
+            cnt += 1
+        blk.append(cnt)
+        total = end
+    c = oracle.pack(total, bs, blk, ll, ml, sr, bytes(lits), tags=False)
+    tags, _ = oracle.min_tags(c)
+    mlen = np.asarray(ml)
+    deferred = mlen[(tags > 0) & (mlen > 0)]
+    assert deferred.size > 5000 and deferred.mean() >= 48
+    for G in (8, 16, 32):
+        check(c, G)
+
+
 # ------------------------------------------------------------ corruption
 
 def test_corrupt_containers_are_rejected_on_upload():
