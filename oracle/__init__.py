@@ -8,13 +8,17 @@ generator ``paper_2607_18541_gb300.synth``.
 ``aclz_oracle.c`` holds the plain sequential definitions (greedy exact-prefix
 chain encoder with distance-class minimum match lengths, Sec. IV-B; the
 sequential decoder; minimal wave tags; validation; chunked FNV-1a; the
-order-0 tile entropy estimate).  This module wraps it with ctypes and adds
-pure-Python brute-force references used to pin it on tiny inputs.
+order-0 tile entropy estimate); ``ans.c`` the tile entropy layer (order-0
+rANS over 64 KiB tiles and the ACLE container of a v1 container's token byte
+planes and literals).  This module wraps both with ctypes and adds
+pure-Python brute-force references used to pin them on tiny inputs.
 
 Parity status: every function here is pinned by tests in
 ``tests/test_oracle.py`` (published FNV vectors, closed forms, brute force,
-round trips, invariants) except ``est_bytes`` beyond its closed-form cases,
-whose absolute scale is a reading of the paper, not something it prints.
+round trips, invariants) and ``tests/test_ans_oracle.py`` (frequency rule
+by hand, closed-form word counts, code-length bounds, round trips), except
+``est_bytes`` beyond its closed-form cases, whose absolute scale is a
+reading of the paper, not something it prints.
 """
 from __future__ import annotations
 
@@ -29,6 +33,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "aclz_oracle.c")
+_SRCS = (_SRC, os.path.join(_HERE, "ans.c"))
 _SO = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -45,9 +50,9 @@ UNLIMITED_WINDOW = (1 << 64) - 1
 
 
 def build(force: bool = False) -> str:
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(map(os.path.getmtime, _SRCS)):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -83,6 +88,16 @@ def lib() -> ctypes.CDLL:
             L.oracle_fnv_chunked.restype = c_u64
             L.oracle_est_bytes.argtypes = [u8p, c_u64, ctypes.POINTER(ctypes.c_double)]
             L.oracle_stats.argtypes = [u8p, c_u64, u64p]
+            L.oracle_ans_quantize.argtypes = [u64p, c_u64, ctypes.POINTER(ctypes.c_uint16)]
+            L.oracle_ans_tile_bound.argtypes = [c_u64]
+            L.oracle_ans_tile_bound.restype = c_u64
+            L.oracle_ans_encode_tile.argtypes = [u8p, c_u32, u8p, c_u64, u64p]
+            L.oracle_ans_decode_tile.argtypes = [u8p, c_u64, u8p, c_u32]
+            L.oracle_acle_bound.argtypes = [u8p, c_u64, u64p]
+            L.oracle_acle_encode.argtypes = [u8p, c_u64, u8p, c_u64, u64p]
+            L.oracle_acle_decoded_size.argtypes = [u8p, c_u64]
+            L.oracle_acle_decoded_size.restype = c_u64
+            L.oracle_acle_decode.argtypes = [u8p, c_u64, u8p, c_u64]
             _lib = L
     return _lib
 
@@ -461,3 +476,112 @@ def simulate_waves(c, order: str = "forward", seed: int = 0) -> np.ndarray:
     if n and (written < 0).any():
         raise OracleError(E_CORRUPT, "simulate_waves: bytes never written")
     return out
+
+
+# ------------------------------------------------------ tile entropy layer
+#
+# ``ans.c``: order-0 interleaved rANS over 64 KiB tiles (32 states, M = 2^12,
+# 16-bit renormalisation), our reading of the paper's tile-ANS entropy layer
+# (Sec. II), and the "ACLE" container that codes a v1 container's 16 token
+# byte planes and literal bytes by tiles.  Pinned in ``tests/test_ans_oracle.py``
+# by round trips, the frequency rules, exact word counts in closed form, the
+# Shannon lower bound and an upper bound on the code length.
+
+ANS_M = 1 << 12
+ANS_L = 1 << 16
+ANS_LANES = 32
+ANS_TILE = 1 << 16
+ANS_TILE_HEADER = 512 + 4 * ANS_LANES + 4
+
+
+def ans_quantize(counts) -> np.ndarray:
+    """Tile frequencies (sum ANS_M) from 256 byte counts."""
+    cnt = np.ascontiguousarray(counts, dtype=np.uint64)
+    if cnt.size != 256:
+        raise OracleError(E_INVAL, "ans_quantize")
+    f = np.zeros(256, dtype=np.uint16)
+    _check(lib().oracle_ans_quantize(cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), int(cnt.sum()),
+                                     f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16))), "ans_quantize")
+    return f
+
+
+def ans_encode_tile(x) -> np.ndarray:
+    """One tile (at most 64 KiB) to its payload: freq[256], state[32], n_words, words."""
+    x = _arr(x)
+    cap = int(lib().oracle_ans_tile_bound(x.size))
+    out = np.zeros(cap, dtype=np.uint8)
+    size = ctypes.c_uint64(0)
+    _check(lib().oracle_ans_encode_tile(_u8(x), x.size, _u8(out), cap, ctypes.byref(size)), "ans_encode_tile")
+    return out[:size.value].copy()
+
+
+def ans_decode_tile(payload, n: int) -> np.ndarray:
+    p = _arr(payload)
+    out = np.zeros(max(1, n), dtype=np.uint8)
+    _check(lib().oracle_ans_decode_tile(_u8(p), p.size, _u8(out), n), "ans_decode_tile")
+    return out[:n]
+
+
+@dataclass
+class AnsTile:
+    freq: np.ndarray    # uint16[256]
+    states: np.ndarray  # uint32[32], the decoder's starting states
+    words: np.ndarray   # uint16, in decode order
+
+
+def ans_tile_fields(payload) -> AnsTile:
+    p = _arr(payload)
+    freq = p[:512].view(np.uint16).copy()
+    states = p[512:512 + 4 * ANS_LANES].view(np.uint32).copy()
+    nw = int(p[512 + 4 * ANS_LANES:ANS_TILE_HEADER].view(np.uint32)[0])
+    words = p[ANS_TILE_HEADER:ANS_TILE_HEADER + 2 * nw].view(np.uint16).copy()
+    return AnsTile(freq, states, words)
+
+
+def acle_encode(c) -> np.ndarray:
+    """The entropy-coded (ACLE) form of a v1 container."""
+    c = _arr(c)
+    bound = ctypes.c_uint64(0)
+    _check(lib().oracle_acle_bound(_u8(c), c.size, ctypes.byref(bound)), "acle_bound")
+    out = np.zeros(bound.value, dtype=np.uint8)
+    size = ctypes.c_uint64(0)
+    _check(lib().oracle_acle_encode(_u8(c), c.size, _u8(out), out.size, ctypes.byref(size)), "acle_encode")
+    return out[:size.value].copy()
+
+
+def acle_decode(e) -> np.ndarray:
+    """The v1 container an ACLE holds."""
+    e = _arr(e)
+    n = int(lib().oracle_acle_decoded_size(_u8(e), e.size))
+    if n == 0:
+        raise OracleError(E_CORRUPT, "acle_decode")
+    out = np.zeros(n, dtype=np.uint8)
+    _check(lib().oracle_acle_decode(_u8(e), e.size, _u8(out), n), "acle_decode")
+    return out
+
+
+@dataclass
+class AcleLayout:
+    size: int
+    prefix: int
+    n_tokens: int
+    n_literals: int
+    n_tiles: int
+    payload_offset: int
+    streams: list       # (length, first tile) per stream: 16 token planes, literals
+    tiles: np.ndarray   # per tile: (payload offset, payload bytes, symbols)
+
+
+def acle_layout(e) -> AcleLayout:
+    e = _arr(e)
+    magic, ver, size, prefix, ns, tile, nt, nl, ntl, po = struct.unpack_from("<4sIQQIIQQQQ", bytes(e[:64]))
+    if magic != b"ACLE" or ver != 1:
+        raise OracleError(E_CORRUPT, "acle_layout")
+    st = 64 + (prefix + 15) // 16 * 16
+    streams = [struct.unpack_from("<QQ", bytes(e[st + 16 * k:st + 16 * k + 16])) for k in range(ns)]
+    tt = st + 16 * ns
+    raw = e[tt:tt + 16 * ntl].view(np.uint32).reshape(-1, 4)
+    tiles = np.stack([raw[:, 0].astype(np.uint64) | (raw[:, 1].astype(np.uint64) << 32),
+                      raw[:, 2].astype(np.uint64), raw[:, 3].astype(np.uint64)], axis=1) if ntl else \
+        np.zeros((0, 3), dtype=np.uint64)
+    return AcleLayout(size, prefix, nt, nl, ntl, po, streams, tiles)
