@@ -144,6 +144,30 @@ int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_handle **ou
 
 int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out);
 
+/* Upload an entropy-coded (ACLE) container and decode its entropy stage on
+ * the GPU, then build the decode index as aclz_upload_ex(flags) does.  The
+ * entropy stage is the one Sec. II puts in front of the match kernel
+ * (entropy decoded over 64 KB tiles by cooperative groups); its coder is
+ * order-0 rANS per 64 KiB tile with frequencies summing to 2^12, 32
+ * interleaved states in [2^16, 2^32) (byte i of a tile on state i mod 32)
+ * and one stream of 16-bit renormalisation words per tile, taken in
+ * increasing lane order within each step of 32 bytes.
+ * Layout (little-endian): a 64-byte header ("ACLE", u32 version 1, u64 size
+ * of the v1 container, u64 raw prefix bytes, u32 streams = 17, u32 tile
+ * size = 65536, u64 n_tokens, u64 n_literals, u64 n_tiles, u64 payload
+ * offset); the v1 header and block directory raw, padded to 16 bytes; per
+ * stream (the 16 byte planes of the token array, plane k = byte k of every
+ * token, then the literal bytes) u64 length and u64 first tile; per tile
+ * u64 payload offset (16-byte aligned, from the payload offset), u32
+ * payload bytes, u32 tile bytes; the payloads: u16 freq[256], u32
+ * state[32], u32 n_words, u16 words[n_words].
+ * host_buf is read during the call only; the handle owns the decoded
+ * tokens and literals (the v1 layout) like any handle.  Synchronizes the
+ * stream.  ACLZ_E_CORRUPT for a malformed ACLE, a tile whose table does
+ * not sum to 2^12, or a tile whose decode does not consume exactly its
+ * words and end every state at 2^16; then as aclz_upload_ex. */
+int aclz_upload_acle(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out);
+
 /* Write the handle's stream back as a host container, with the wave tags
  * the upload computed (flag and n_waves set, per-block max wave in the
  * directory), so a later upload of it only checks the tags, in parallel,

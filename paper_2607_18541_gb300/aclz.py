@@ -81,6 +81,7 @@ _SIGS = [
     ("aclz_container_info", _I, [_VP, _U64, ctypes.POINTER(aclz_info)]),
     ("aclz_upload", _I, [_VP, _U64, _VP, ctypes.POINTER(_VP)]),
     ("aclz_upload_ex", _I, [_VP, _U64, _U32, _VP, ctypes.POINTER(_VP)]),
+    ("aclz_upload_acle", _I, [_VP, _U64, _U32, _VP, ctypes.POINTER(_VP)]),
     ("aclz_free", _I, [_VP]),
     ("aclz_handle_info", _I, [_VP, ctypes.POINTER(aclz_info)]),
     ("aclz_wave_counts", _I, [_VP, _U64P, _U32]),
@@ -237,6 +238,15 @@ def aclz_upload(buf, stream=None, flags: int = 0) -> int:
         _ck(lib().aclz_upload_ex(_hptr(c), c.size, flags, _stream(stream), ctypes.byref(h)), "aclz_upload_ex")
     else:
         _ck(lib().aclz_upload(_hptr(c), c.size, _stream(stream), ctypes.byref(h)), "aclz_upload")
+    return int(h.value)
+
+
+def aclz_upload_acle(buf, stream=None, flags: int = 0) -> int:
+    """Upload an entropy-coded (ACLE) container; its tiles are decoded on
+    the GPU.  Returns the handle as an integer."""
+    e = _np_u8(buf)
+    h = ctypes.c_void_p(0)
+    _ck(lib().aclz_upload_acle(_hptr(e), e.size, flags, _stream(stream), ctypes.byref(h)), "aclz_upload_acle")
     return int(h.value)
 
 

@@ -717,14 +717,23 @@ extern "C" int aclz_upload(const void *host_buf, uint64_t n, void *stream, aclz_
     return aclz_upload_ex(host_buf, n, 0, stream, out);
 }
 
-extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out) {
+namespace aclz {
+
+// Token array and literal bytes of a host container: copied as they are.
+static int fill_from_host(aclz_handle *h, const View &v, const void *, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (v.n_tokens && cudaMemcpyAsync(h->d_tok, v.tok, kTok * v.n_tokens, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return ACLZ_E_CUDA;
+    if (v.n_literals && cudaMemcpyAsync(h->d_lit, v.lit, v.n_literals, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return ACLZ_E_CUDA;
+    return ACLZ_OK;
+}
+
+int upload_view(const View &v, uint32_t flags, void *stream, FillFn fill, const void *ctx, aclz_handle **out) {
     if (flags & ~(uint32_t)ACLZ_UPLOAD_FLATTEN) return ACLZ_E_INVAL;
     const bool flat_up = (flags & ACLZ_UPLOAD_FLATTEN) != 0;
-    if (!host_buf || !out) return ACLZ_E_INVAL;
+    if (!out) return ACLZ_E_INVAL;
     *out = nullptr;
-    View v;
-    int rc = parse_container((const uint8_t *)host_buf, n, &v, true);
-    if (rc) return rc;
     if (!is_pow2(v.block_size) || v.block_size < kMinBlock || v.block_size > kMaxBlock)
         return ACLZ_E_UNSUPPORTED;
     if (v.n_tokens >= 0xffffffffULL) return ACLZ_E_UNSUPPORTED;
@@ -757,8 +766,10 @@ extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, 
     CK(cudaMalloc((void **)&h->d_err, 64));
     CK(cudaMemsetAsync(h->d_err, 0, 64, st));
     CK(cudaMemsetAsync(h->d_lit + v.n_literals, 0, 32, st));
-    if (nt) CK(cudaMemcpyAsync(h->d_tok, v.tok, kTok * nt, cudaMemcpyHostToDevice, st));
-    if (v.n_literals) CK(cudaMemcpyAsync(h->d_lit, v.lit, v.n_literals, cudaMemcpyHostToDevice, st));
+    if (int rc = fill(h, v, ctx, stream); rc != ACLZ_OK) {
+        cleanup();
+        return rc;
+    }
     CK(cudaMemcpyAsync(h->d_blk_tok, bt.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(h->d_blk_lit, bl.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, st));
     if (nb == 0) {
@@ -768,7 +779,7 @@ extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, 
         *out = h;
         return ACLZ_OK;
     }
-    rc = build_index(h, (v.flags & kFlagWaves) != 0, v.n_waves, flat_up, stream);
+    int rc = build_index(h, (v.flags & kFlagWaves) != 0, v.n_waves, flat_up, stream);
     if (rc) { cleanup(); return rc; }
     if (flat_up || h->needs_flatten) {
         rc = aclz_flatten(h, stream);
@@ -776,6 +787,18 @@ extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, 
     }
     *out = h;
     return ACLZ_OK;
+}
+
+}  // namespace aclz
+
+extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out) {
+    if (flags & ~(uint32_t)ACLZ_UPLOAD_FLATTEN) return ACLZ_E_INVAL;
+    if (!host_buf || !out) return ACLZ_E_INVAL;
+    *out = nullptr;
+    View v;
+    int rc = parse_container((const uint8_t *)host_buf, n, &v, true);
+    if (rc) return rc;
+    return upload_view(v, flags, stream, fill_from_host, nullptr, out);
 }
 
 extern "C" int aclz_free(aclz_handle *h) {

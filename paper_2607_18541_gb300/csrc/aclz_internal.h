@@ -69,6 +69,13 @@ namespace aclz {
 // worklists, schedule); see aclz_index.cu.
 int build_index(aclz_handle *h, bool has_tags, uint32_t given_waves, bool flat_local, void *stream);
 
+// Upload from a parsed container view: allocates the handle's arrays, has
+// fill(h, v, ctx, stream) place the token array in h->d_tok and the literal
+// bytes in h->d_lit (stream-ordered), then builds the decode index as
+// aclz_upload_ex does.
+using FillFn = int (*)(aclz_handle *h, const View &v, const void *ctx, void *stream);
+int upload_view(const View &v, uint32_t flags, void *stream, FillFn fill, const void *ctx, aclz_handle **out);
+
 // Matches per work range for a target byte size of deferred matches.
 inline uint32_t range_matches(uint32_t range_bytes, double mean_len) {
     double t = mean_len > 0 ? (double)range_bytes / mean_len : 16.0;
