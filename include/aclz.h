@@ -168,6 +168,20 @@ int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *strea
  * words and end every state at 2^16; then as aclz_upload_ex. */
 int aclz_upload_acle(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out);
 
+/* Host side of the entropy stage: the ACLE form (layout above) of the v1
+ * container host_container[0, n).  Each 64 KiB tile of each stream is coded
+ * on its own (frequencies: the only byte value present takes all of 2^12;
+ * otherwise each present value max(1, floor(count * 2^12 / n)), the
+ * difference to 2^12 settled on the largest frequency, lowest byte value
+ * first), so the tiles are coded in parallel on `threads` host threads
+ * (0: all hardware threads); the output does not depend on the thread
+ * count.  aclz_acle_bound gives the largest size the call can write.
+ * ACLZ_E_CORRUPT for an invalid v1 container, ACLZ_E_CAPACITY when cap is
+ * too small (nothing written past cap). */
+int aclz_acle_bound(const void *host_container, uint64_t n, uint64_t *out);
+int aclz_acle_encode(const void *host_container, uint64_t n, int threads, void *host_out, uint64_t cap,
+                     uint64_t *out_size);
+
 /* Write the handle's stream back as a host container, with the wave tags
  * the upload computed (flag and n_waves set, per-block max wave in the
  * directory), so a later upload of it only checks the tags, in parallel,

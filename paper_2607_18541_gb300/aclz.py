@@ -82,6 +82,8 @@ _SIGS = [
     ("aclz_upload", _I, [_VP, _U64, _VP, ctypes.POINTER(_VP)]),
     ("aclz_upload_ex", _I, [_VP, _U64, _U32, _VP, ctypes.POINTER(_VP)]),
     ("aclz_upload_acle", _I, [_VP, _U64, _U32, _VP, ctypes.POINTER(_VP)]),
+    ("aclz_acle_bound", _I, [_VP, _U64, ctypes.POINTER(_U64)]),
+    ("aclz_acle_encode", _I, [_VP, _U64, _I, _VP, _U64, ctypes.POINTER(_U64)]),
     ("aclz_free", _I, [_VP]),
     ("aclz_handle_info", _I, [_VP, ctypes.POINTER(aclz_info)]),
     ("aclz_wave_counts", _I, [_VP, _U64P, _U32]),
@@ -248,6 +250,18 @@ def aclz_upload_acle(buf, stream=None, flags: int = 0) -> int:
     h = ctypes.c_void_p(0)
     _ck(lib().aclz_upload_acle(_hptr(e), e.size, flags, _stream(stream), ctypes.byref(h)), "aclz_upload_acle")
     return int(h.value)
+
+
+def aclz_acle_encode(buf, threads: int = 0) -> np.ndarray:
+    """The entropy-coded (ACLE) form of a host v1 container."""
+    c = _np_u8(buf)
+    bound = ctypes.c_uint64(0)
+    _ck(lib().aclz_acle_bound(_hptr(c), c.size, ctypes.byref(bound)), "aclz_acle_bound")
+    out = np.empty(bound.value, dtype=np.uint8)
+    size = ctypes.c_uint64(0)
+    _ck(lib().aclz_acle_encode(_hptr(c), c.size, threads, _hptr(out), out.size, ctypes.byref(size)),
+        "aclz_acle_encode")
+    return out[:size.value]
 
 
 def aclz_free(h: int) -> None:

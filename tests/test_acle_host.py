@@ -3,6 +3,8 @@ or unknown flags are refused before any device work, with ACLZ_E_CORRUPT or
 ACLZ_E_INVAL.  The checks cover the header, the stream and tile tables, the
 payload bounds and every tile's frequency table and word count; the GPU
 parity of accepted containers is in test_gpu_ans.py."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -71,3 +73,40 @@ def test_unknown_flags_are_refused(acle):
     with pytest.raises(aclz.AclzError) as ex:
         aclz.aclz_upload_acle(e, None, flags=4)
     assert ex.value.code == aclz.ACLZ_E_INVAL
+
+
+@functools.lru_cache(maxsize=1)
+def _containers():
+    return {
+        "markov": oracle.encode(synth.markov2(1 << 20, seed=32), 1 << 16),
+        "fastq_tuned": oracle.encode(synth.fastq(1 << 20, seed=33), 1 << 14, oracle.PRESET_TUNED),
+        "sweep32_tagged": oracle.pack_sweep(synth.copy_sweep(4 << 20, 1 << 15, 32), tags=True),
+        "literal_only": oracle.encode(np.frombuffer(np.random.default_rng(3).bytes(150_000), np.uint8), 1 << 12),
+        "empty": oracle.encode(np.zeros(0, np.uint8), 1 << 12),
+    }
+
+
+@pytest.mark.parametrize("name", ["markov", "fastq_tuned", "sweep32_tagged", "literal_only", "empty"])
+@pytest.mark.parametrize("threads", [0, 1, 3])
+def test_library_acle_encoder_writes_the_oracles_bytes(name, threads):
+    # the format fixes every byte (tables, states, word order, padding), so
+    # the library's encoder and the oracle's must agree exactly
+    c = _containers()[name]
+    e = aclz.aclz_acle_encode(c, threads=threads)
+    assert np.array_equal(e, oracle.acle_encode(c))
+    assert np.array_equal(oracle.acle_decode(e), c)
+
+
+def test_library_acle_encoder_refuses_bad_input():
+    c = oracle.encode(synth.markov2(100_000, seed=34), 1 << 14)
+    bad = c.copy()
+    bad[:4] = np.frombuffer(b"ACLE", np.uint8)
+    with pytest.raises(aclz.AclzError) as ex:
+        aclz.aclz_acle_encode(bad)
+    assert ex.value.code == aclz.ACLZ_E_CORRUPT
+    bound = aclz.ctypes.c_uint64(0)
+    assert aclz.lib().aclz_acle_bound(aclz._hptr(c), c.size, aclz.ctypes.byref(bound)) == 0
+    out = np.zeros(64, np.uint8)
+    size = aclz.ctypes.c_uint64(0)
+    rc = aclz.lib().aclz_acle_encode(aclz._hptr(c), c.size, 0, aclz._hptr(out), out.size, aclz.ctypes.byref(size))
+    assert rc == aclz.ACLZ_E_CAPACITY and bound.value > out.size
