@@ -93,6 +93,10 @@ def lib() -> ctypes.CDLL:
                                            ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u32p, u64p,
                                            ctypes.c_uint64, u8p, ctypes.c_uint64, u64p]
             L.synth_copy_sweep.restype = ctypes.c_int64
+            L.synth_copy_sweep_lengths.argtypes = [ctypes.c_uint64, ctypes.c_uint32, u32p, ctypes.c_uint64,
+                                                   ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u32p, u64p,
+                                                   ctypes.c_uint64, u8p, ctypes.c_uint64, u64p]
+            L.synth_copy_sweep_lengths.restype = ctypes.c_int64
             L.synth_stream_sizes.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
                                              ctypes.c_uint64, u64p, u64p]
             L.synth_stream_sizes.restype = ctypes.c_int
@@ -227,6 +231,32 @@ def copy_sweep(total: int, block_size: int, L: int, lit_mean: int = 4,
     _check(int(nt), "copy_sweep")
     nt = int(nt)
     return CopySweep(total, block_size, L, lit_mean, seed, blk, ll[:nt].copy(), ml[:nt].copy(),
+                     sr[:nt].copy(), lits[:int(nlit[0])].copy())
+
+
+def copy_sweep_lengths(total: int, block_size: int, lengths, lit_mean: int = 4,
+                       seed: int = SEED_COPY) -> CopySweep:
+    """The copy sweep with every match length drawn uniformly from
+    `lengths` (e.g. the match lengths of an encoded stream: its empirical
+    distribution) instead of one fixed L."""
+    table = np.ascontiguousarray(lengths, dtype=np.uint32)
+    if table.size == 0 or int(table.min()) == 0:
+        raise ValueError("lengths must be non-empty and positive")
+    nb = (total + block_size - 1) // block_size
+    cap = total // int(table.min()) + nb + 1
+    blk = np.zeros(nb, dtype=np.uint32)
+    ll = np.empty(cap, dtype=np.uint32)
+    ml = np.empty(cap, dtype=np.uint32)
+    sr = np.empty(cap, dtype=np.uint64)
+    lits = np.empty(max(total, 1), dtype=np.uint8)
+    nlit = np.zeros(1, dtype=np.uint64)
+    nt = lib().synth_copy_sweep_lengths(total, block_size, _ptr(table, ctypes.c_uint32), table.size, lit_mean,
+                                        seed, _ptr(blk, ctypes.c_uint32), _ptr(ll, ctypes.c_uint32),
+                                        _ptr(ml, ctypes.c_uint32), _ptr(sr, ctypes.c_uint64), cap,
+                                        _ptr(lits, ctypes.c_uint8), total, _ptr(nlit, ctypes.c_uint64))
+    _check(int(nt), "copy_sweep_lengths")
+    nt = int(nt)
+    return CopySweep(total, block_size, 0, lit_mean, seed, blk, ll[:nt].copy(), ml[:nt].copy(),
                      sr[:nt].copy(), lits[:int(nlit[0])].copy())
 
 

@@ -507,12 +507,14 @@ int synth_wordtext(uint8_t *out, uint64_t n, uint64_t seed, uint64_t chunk_bytes
  * Otherwise the block is finished by one literal-only token holding all its
  * remaining bytes.  Arrays are caller-allocated; returns the token count or
  * a negative error. */
-int64_t synth_copy_sweep(uint64_t total, uint32_t block_size, uint32_t L, uint32_t lit_mean,
-                         uint64_t seed, uint32_t *blk_ntok, uint32_t *lit_len, uint32_t *match_len,
-                         uint64_t *src, uint64_t tok_cap, uint8_t *literals, uint64_t lit_cap,
-                         uint64_t *out_nlit) {
-    if (block_size == 0 || L == 0 || !blk_ntok || !lit_len || !match_len || !src || !out_nlit)
+static int64_t copy_sweep_table(uint64_t total, uint32_t block_size, const uint32_t *table, uint64_t n_table,
+                                uint32_t lit_mean, uint64_t seed, uint32_t *blk_ntok, uint32_t *lit_len,
+                                uint32_t *match_len, uint64_t *src, uint64_t tok_cap, uint8_t *literals,
+                                uint64_t lit_cap, uint64_t *out_nlit) {
+    if (block_size == 0 || !table || n_table == 0 || !blk_ntok || !lit_len || !match_len || !src || !out_nlit)
         return SYNTH_E_INVAL;
+    for (uint64_t k = 0; k < n_table; k++)
+        if (table[k] == 0) return SYNTH_E_INVAL;
     synth_rng r;
     rng_seed(&r, seed);
     uint64_t nb = (total + block_size - 1) / block_size;
@@ -524,13 +526,15 @@ int64_t synth_copy_sweep(uint64_t total, uint32_t block_size, uint32_t L, uint32
         uint32_t cnt = 0;
         while (pos < bend) {
             uint64_t lit = geom0(&r, lit_mean);
+            /* a one-entry table draws nothing: the fixed-length sweep */
+            const uint64_t L = n_table == 1 ? table[0] : table[rng_below(&r, n_table)];
             uint64_t mpos = pos + lit;
             if (mpos > L && mpos + L <= bend) {
                 if (nt >= tok_cap || nl + lit > lit_cap) return SYNTH_E_CAPACITY;
                 for (uint64_t i = 0; i < lit; i++) literals[nl + i] = (uint8_t)(rng_next(&r) >> 56);
                 nl += lit;
                 lit_len[nt] = (uint32_t)lit;
-                match_len[nt] = L;
+                match_len[nt] = (uint32_t)L;
                 src[nt] = rng_below(&r, mpos - L);
                 nt++;
                 cnt++;
@@ -552,6 +556,27 @@ int64_t synth_copy_sweep(uint64_t total, uint32_t block_size, uint32_t L, uint32
     }
     *out_nlit = nl;
     return (int64_t)nt;
+}
+
+int64_t synth_copy_sweep(uint64_t total, uint32_t block_size, uint32_t L, uint32_t lit_mean,
+                         uint64_t seed, uint32_t *blk_ntok, uint32_t *lit_len, uint32_t *match_len,
+                         uint64_t *src, uint64_t tok_cap, uint8_t *literals, uint64_t lit_cap,
+                         uint64_t *out_nlit) {
+    const uint32_t table[1] = {L};
+    if (L == 0) return SYNTH_E_INVAL;
+    return copy_sweep_table(total, block_size, table, 1, lit_mean, seed, blk_ntok, lit_len, match_len, src,
+                            tok_cap, literals, lit_cap, out_nlit);
+}
+
+/* The copy sweep with each match length drawn uniformly from table[0, n)
+ * (an empirical match-length distribution) instead of a fixed L; a length
+ * that does not fit ends the block with literals, as a fixed L does. */
+int64_t synth_copy_sweep_lengths(uint64_t total, uint32_t block_size, const uint32_t *table, uint64_t n_table,
+                                 uint32_t lit_mean, uint64_t seed, uint32_t *blk_ntok, uint32_t *lit_len,
+                                 uint32_t *match_len, uint64_t *src, uint64_t tok_cap, uint8_t *literals,
+                                 uint64_t lit_cap, uint64_t *out_nlit) {
+    return copy_sweep_table(total, block_size, table, n_table, lit_mean, seed, blk_ntok, lit_len, match_len, src,
+                            tok_cap, literals, lit_cap, out_nlit);
 }
 
 /* ====================================================== batched workload */
