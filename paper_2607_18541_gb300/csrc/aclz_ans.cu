@@ -198,8 +198,11 @@ extern "C" int aclz_upload_acle(const void *host_buf, uint64_t n, uint32_t flags
     if (rd32le(e + 24) != kStreams || rd32le(e + 28) != kTile) return ACLZ_E_CORRUPT;
     if (prefix < 64 || prefix > n - 64 || n_tok > size / 16 || n_lit > size || prefix + 16 * n_tok + n_lit != size)
         return ACLZ_E_CORRUPT;
+    // the raw v1 header and directory (tokens and literals come from the
+    // tiles): the directory must lie inside the stored prefix before it is
+    // walked, since the v1 size above only says what the fields claim
+    if (64 + 32 * (uint64_t)rd32le(e + 64 + 20) != prefix) return ACLZ_E_CORRUPT;
     View v;
-    // the raw v1 header and directory; tokens and literals come from the tiles
     int rc = parse_container(e + 64, size, &v, true);
     if (rc) return rc;
     if (64 + 32 * (uint64_t)v.n_blocks != prefix || v.n_tokens != n_tok || v.n_literals != n_lit)

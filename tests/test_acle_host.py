@@ -54,12 +54,27 @@ def _variants(e, lay):
     b = e.copy(); f = b[first:first + 512].view(np.uint16); f[int(np.argmax(f))] += 1; out["table_sum"] = b
     b = e.copy(); b[first + 640:first + 644] = _u32(1); out["word_count"] = b
     b = e.copy(); b[64 + 20:64 + 24] = _u32(3); out["v1_directory"] = b   # n_blocks of the raw v1 header
+    # fields that all agree on a directory far longer than the buffer: the
+    # raw header claims 2^20 blocks, and the v1 size and literal counts
+    # (ACLE header and raw header) are set to match it, so only the stored
+    # prefix length shows that the directory is not in the buffer
+    b = e.copy()
+    bs = int(b[64 + 16:64 + 20].view(np.uint32)[0])
+    nb = 1 << 20
+    size = 64 + 32 * nb + 16 * lay.n_tokens + (1 << 30)
+    b[8:16] = _u64(size)
+    b[40:48] = _u64(size - lay.prefix - 16 * lay.n_tokens)
+    b[64 + 8:64 + 16] = _u64(bs * nb)
+    b[64 + 20:64 + 24] = _u32(nb)
+    b[64 + 32:64 + 40] = _u64(1 << 30)
+    out["directory_beyond_buffer"] = b
     return out
 
 
 @pytest.mark.parametrize("name", ["magic", "version", "short", "truncated_tables", "v1_size", "n_streams",
                                   "tile_size", "n_tiles", "stream_length", "tile_bytes", "unaligned_payload",
-                                  "payload_out_of_range", "table_sum", "word_count", "v1_directory"])
+                                  "payload_out_of_range", "table_sum", "word_count", "v1_directory",
+                                  "directory_beyond_buffer"])
 def test_malformed_acle_is_refused_on_the_host(acle, name):
     e, lay = acle
     bad = _variants(e, lay)[name]
@@ -110,3 +125,16 @@ def test_library_acle_encoder_refuses_bad_input():
     size = aclz.ctypes.c_uint64(0)
     rc = aclz.lib().aclz_acle_encode(aclz._hptr(c), c.size, 0, aclz._hptr(out), out.size, aclz.ctypes.byref(size))
     assert rc == aclz.ACLZ_E_CAPACITY and bound.value > out.size
+
+
+@pytest.mark.parametrize("name", ["markov", "empty"])
+def test_valid_acle_passes_the_host_checks(name):
+    # on a machine without a GPU the call then fails at device allocation,
+    # never as a malformed container; with one it uploads
+    e = aclz.aclz_acle_encode(_containers()[name])
+    try:
+        h = aclz.aclz_upload_acle(e, None)
+    except aclz.AclzError as ex:
+        assert ex.code not in (aclz.ACLZ_E_CORRUPT, aclz.ACLZ_E_INVAL)
+    else:
+        aclz.aclz_free(h)
