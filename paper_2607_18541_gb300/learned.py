@@ -362,7 +362,7 @@ def training_streams(scale: int = 1):
 
 # ------------------------------------------------------------ gain benchmark
 
-def _decode_gbs(c, n: int, reps: int = 5, flatten: bool = False, **cfg):
+def decode_gbs(c, n: int, reps: int = 5, flatten: bool = False, **cfg):
     """(median output GB/s of decode_all, output equals the input) for one
     container, optionally uploaded with the flattened two-wave schedule."""
     import torch
@@ -421,12 +421,12 @@ def gain_single(model: Model, x, block_size: int = BLOCK, reps: int = 5, bound: 
         rows_c.append(("label bound", encode_learned(Choices(yb), x, block_size, base=base, fb=fb)[0]))
     for name, c in rows_c:
         try:
-            gbs, out = _decode_gbs(c, x.size, reps)
+            gbs, out = decode_gbs(c, x.size, reps)
             ok = bool(torch.equal(out, xd))
             gbs = round(gbs, 1)
         except aclz.AclzError as e:  # e.g. a wave table too large for the plain schedule
             gbs, ok = str(e), True
-        gbs_f, out = _decode_gbs(c, x.size, reps, flatten=True)
+        gbs_f, out = decode_gbs(c, x.size, reps, flatten=True)
         rows.append(dict(thresholds=name, bytes=int(x.size), est_ratio=round(x.size / est_bytes(c), 4),
                          tokens=int(read_tokens(c)[0].sum()), decode_gbs=gbs,
                          flattened_decode_gbs=round(gbs_f, 1), exact=ok and bool(torch.equal(out, xd))))

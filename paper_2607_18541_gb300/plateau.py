@@ -61,7 +61,7 @@ def run(mib: int, sweep_mib: int, block_size: int, mm, gpu: bool):
         for r, cont, n, ref in ((rows[0], c, x.size, x), (rows[1], _container(hist), hist.total, None),
                                 (rows[2], _container(fixed), fixed.total, None)):
             for flat in (False, True):
-                gbs, out = learned._decode_gbs(cont, n, flatten=flat)
+                gbs, out = learned.decode_gbs(cont, n, flatten=flat)
                 if ref is not None and not np.array_equal(out.cpu().numpy(), ref):
                     raise RuntimeError("decode differs from the input")
                 r["decode_gbs_flattened" if flat else "decode_gbs"] = round(gbs, 1)

@@ -56,7 +56,7 @@ def row(x: np.ndarray, mm, block_size: int, gpu: bool) -> dict:
          "mean_match_len": round(float(ml[m].mean()), 2) if m.any() else 0.0}
     if gpu:
         for flat in (False, True):
-            gbs, out = learned._decode_gbs(c, x.size, flatten=flat)
+            gbs, out = learned.decode_gbs(c, x.size, flatten=flat)
             if not np.array_equal(out.cpu().numpy(), x):
                 raise RuntimeError("decode differs from the input")
             r["decode_gbs_flattened" if flat else "decode_gbs"] = round(gbs, 1)
