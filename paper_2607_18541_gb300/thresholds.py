@@ -11,7 +11,7 @@ estimate), the order-0 estimate of the same container, tokens, matches and
 their mean length, and, on a GPU, the decode throughput of the plain and
 the flattened schedules.
 
-    python -m paper_2607_18541_gb300.thresholds [--mib 64] [--gpu]
+    python -m paper_2607_18541_gb300.thresholds [--mib 64] [--gpu] [--streams fastq] [--presets-only]
 """
 from __future__ import annotations
 
@@ -68,10 +68,15 @@ def main():
     ap.add_argument("--mib", type=int, default=64)
     ap.add_argument("--block-size", type=int, default=1 << 14)
     ap.add_argument("--gpu", action="store_true", help="also time the decode on the current GPU")
+    ap.add_argument("--streams", default="fastq,markov,wordtext", help="comma-separated subset")
+    ap.add_argument("--presets-only", action="store_true", help="skip the band sweep")
     args = ap.parse_args()
+    want = set(args.streams.split(","))
     for name, make in streams(args.mib):
+        if name not in want:
+            continue
         x = make()
-        for vname, mm in variants():
+        for vname, mm in variants()[:3] if args.presets_only else variants():
             r = {"stream": name, "mib": args.mib, "block_size": args.block_size, "variant": vname}
             r.update(row(x, mm, args.block_size, args.gpu))
             print(json.dumps(r), flush=True)
