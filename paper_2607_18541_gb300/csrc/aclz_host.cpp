@@ -68,7 +68,10 @@ bool build_prev(const uint8_t *x, uint64_t n, uint32_t *prev, int threads) {
             uint64_t s = (h >> 20) & (cap - 1);
             while (last[s] != ~0ULL && keys[s] != k) s = (s + 1) & (cap - 1);
             if (last[s] == ~0ULL) {
+                // a new key: stored with its position before any growth, so
+                // the rehash carries it over
                 keys[s] = k;
+                last[s] = p;
                 prev[p] = 0;
                 if (++used * 2 > cap) {
                     // grow and rehash
@@ -85,13 +88,11 @@ bool build_prev(const uint8_t *x, uint64_t n, uint32_t *prev, int threads) {
                     keys.swap(nk);
                     last.swap(nl);
                     cap = ncap;
-                    s = (h >> 20) & (cap - 1);
-                    while (last[s] != ~0ULL && keys[s] != k) s = (s + 1) & (cap - 1);
                 }
-            } else {
-                uint64_t d = p - last[s];
-                prev[p] = d < (1ULL << 32) ? (uint32_t)d : 0;
+                continue;
             }
+            const uint64_t d = p - last[s];
+            prev[p] = d < (1ULL << 32) ? (uint32_t)d : 0;
             last[s] = p;
         }
     };
@@ -127,6 +128,9 @@ void parse_block(const uint8_t *x, uint64_t n, uint64_t bstart, uint64_t bend, c
                 uint64_t lim = std::min<uint64_t>(d, bend - p);
                 uint64_t need = T[dclass(d)];
                 if (lim < need || lim <= best) continue;
+                // only a longer match replaces the best, so the byte at
+                // offset best must agree (best < lim keeps it in range)
+                if (best && x[q + best] != x[p + best]) continue;
                 // compare 8 bytes at a time
                 uint64_t len = 0;
                 while (len + 8 <= lim) {
@@ -143,7 +147,11 @@ void parse_block(const uint8_t *x, uint64_t n, uint64_t bstart, uint64_t bend, c
                 while (len < lim && x[q + len] == x[p + len]) len++;
             done:
                 if (len > lim) len = lim;
-                if (len >= need && len > best) { best = len; bsrc = q; }
+                if (len >= need && len > best) {
+                    best = len;
+                    bsrc = q;
+                    if (best == bend - p) break;  // nothing can be longer
+                }
             }
         }
         if (best) {
