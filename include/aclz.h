@@ -147,7 +147,7 @@ int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *strea
 /* Upload an entropy-coded (ACLE) container and decode its entropy stage on
  * the GPU, then build the decode index as aclz_upload_ex(flags) does.  The
  * entropy stage is the one Sec. II puts in front of the match kernel
- * (entropy decoded over 64 KB tiles by cooperative groups); its coder is
+ * (an ANS stage on 64 KB tiles, many at once); its coder is
  * order-0 rANS per 64 KiB tile with frequencies summing to 2^12, 32
  * interleaved states in [2^16, 2^32) (byte i of a tile on state i mod 32)
  * and one stream of 16-bit renormalisation words per tile, taken in

@@ -1,7 +1,8 @@
 /* Tile entropy layer of the CPU oracle (test infrastructure only).
  *
- * The paper's pipeline decodes entropy over 64 KB tiles before the match
- * phase ("tile-ANS", Sec. II); it gives no coder parameters.  Our reading:
+ * In the paper's pipeline an ANS entropy stage works on 64 KB tiles, many
+ * at once, ahead of the match kernel (Sec. II), with no coder parameters
+ * given.  Our reading:
  *
  *  - every byte stream is cut into tiles of 65536 bytes (the last shorter);
  *  - each tile is coded on its own with an order-0 range-variant asymmetric

@@ -1,14 +1,13 @@
 // Host encoder of the tile entropy stage: the ACLE form of a v1 container
 // (the layout and coder are those aclz_upload_acle decodes; see aclz.h).
 //
-// The paper's pipeline entropy-codes the stream over 64 KB tiles
-// ("tile-ANS", Sec. II) and decodes them on the GPU before the match
-// phase; it gives no coder parameters.  Here each tile is coded on its own
-// with order-0 rANS: the tile's byte counts are scaled to frequencies that
-// sum to 2^12, 32 coder states share the tile (byte i on state i mod 32),
-// and a state that would leave [2^16, 2^32) while coding gives up its low 16
-// bits as a word.  Tiles are independent, so they are coded in parallel on
-// the host threads.
+// In the paper's pipeline an ANS stage works on 64 KB tiles on the GPU
+// ahead of the match phase (Sec. II); no coder parameters are given.  Here
+// each tile is coded on its own with order-0 rANS: the tile's byte counts
+// are scaled to frequencies that sum to 2^12, 32 coder states share the
+// tile (byte i on state i mod 32), and a state that would leave
+// [2^16, 2^32) while coding gives up its low 16 bits as a word.  Tiles are
+// independent, so they are coded in parallel on the host threads.
 #include <algorithm>
 #include <atomic>
 #include <cstring>

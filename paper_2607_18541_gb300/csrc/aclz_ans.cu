@@ -1,5 +1,5 @@
-// Tile entropy stage in front of the match phase (Sec. II: entropy is
-// decoded over 64 KB tiles by cooperative groups before the match kernel).
+// Tile entropy stage in front of the match phase (Sec. II places an ANS
+// stage on 64 KB tiles, many in parallel, ahead of the match kernel).
 //
 // An ACLE container holds a v1 container's header and block directory raw
 // and its 16 token byte planes and literal bytes as order-0 rANS tiles of
