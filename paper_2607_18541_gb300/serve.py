@@ -10,9 +10,9 @@ several CUDA streams, so batches that arrive while others run overlap on the
 device.  Completion times come from CUDA events, so latency = GPU completion
 - arrival, on one clock.
 
-The paper's seek is random access into GPU-resident compressed data without
-whole-file decompression (abstract; Sec. I); this loop serves many such
-accesses at once.
+In the paper a seek reads any region of a stream that stays compressed in
+GPU memory, decoding only that region (abstract; Sec. I); this loop serves
+many such region reads at once.
 """
 from __future__ import annotations
 
