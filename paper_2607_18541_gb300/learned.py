@@ -1,7 +1,7 @@
 """Learned per-block minimum-match thresholds.
 
-The paper's lever (Sec. IV-B) raises the minimum match length by distance
-class from 6/8/10/12 to 12/16/24/32 for a whole stream; its cause (Sec.
+The paper's lever (Sec. IV-B) lifts the per-distance-class floor on match
+lengths from 6/8/10/12 to 12/16/24/32 for a whole stream; its cause (Sec.
 IV-C) is that short matches to far offsets cost more offset bits than they
 save and leave the decoding warp underloaded.  Here a small network picks,
 for each 16 KiB block, one of K candidate vectors, with 12/16/24/32 as the
