@@ -3,8 +3,8 @@
  * GB300 (sm_103a).  C ABI of libaclz.so.
  *
  * The codec follows the paper "What Governs Decode Throughput in
- * Absolute-Offset GPU LZ77?": back-references are absolute output positions
- * (abstract; Sec. I), LZ blocks fixed at encode time are the unit of decode
+ * Absolute-Offset GPU LZ77?": every back-reference names an absolute
+ * position of the output (abstract; Sec. I), LZ blocks fixed at encode time are the unit of decode
  * parallelism (Sec. II), minimum match lengths are set per distance class
  * (Sec. IV-B), matches whose sources are not yet written are decoded in
  * later waves (Sec. I), and results are verified by byte compare and FNV

@@ -12,7 +12,7 @@
  *    (abstract; Sec. II);
  *  - LZ blocks set at encode time are the unit of decode parallelism
  *    (Sec. II, Sec. V);
- *  - minimum match length by distance class, bands d < 128, < 16384,
+ *  - a floor on match length per distance class, bands d < 128, < 16384,
  *    < 2097152, >= 2097152, presets 6/8/10/12 and 12/16/24/32 (Sec. IV-B),
  *    and 16/24/32/48 (Sec. IV-C);
  *  - wavefront decode of matches whose sources are not yet written (Sec. I,

@@ -2,9 +2,9 @@
 block size and the lanes per SM (resident CTAs per SM of the persistent
 launch, and the size of its work ranges).
 
-The paper's effective-workload law (Sec. III-A, Table I) says throughput is
-a function of lanes = G x N_blocks: starved below ~32K lanes, about half of
-saturated near 65K, saturated above ~1M.  The tuner ranks the candidate
+The paper's effective-workload law (Sec. III-A, Table I) ties throughput
+to lanes = G x N_blocks: starved below ~32K lanes, about half of saturated
+near 65K, saturated above ~1M.  The tuner ranks the candidate
 (G, block size) pairs by that law, measures the most promising ones on the
 GPU (CUDA events, median of several decodes), and returns the fastest.
 """

@@ -3,9 +3,9 @@
 // with these kernels.
 //
 // The paper's lever (Sec. IV-B, IV-C) is a fixed vector of minimum match
-// lengths by distance class; its cause (Sec. IV-C) is that a short match to
-// a far offset costs more bits than it saves and also starves the decoding
-// warp.  The network picks, per block, one of K candidate vectors from
+// lengths by distance class; its cause (Sec. IV-C) is that short copies
+// from distant positions cost more in offset bits than the literals they
+// replace, and give the decoding warp too little work.  The network picks, per block, one of K candidate vectors from
 // statistics of the block, so blocks can take a different point on that
 // trade-off.  Sizes are tiny (6.5k parameters), so the contractions run on
 // CUDA cores; tiles of 32 samples keep activations in shared memory and

@@ -1,8 +1,8 @@
 // Range decode (seek): out = decode(x)[lo, hi) without decoding the rest.
 //
 // Absolute back-references make any output byte resolvable on its own
-// (abstract; Sec. I: random access into compressed data without whole-file
-// decompression).  A byte inside a match at position p comes from
+// (abstract; Sec. I: a region of the stream can be read without decoding
+// the whole of it).  A byte inside a match at position p comes from
 // src + (p - dst); following that chain always moves strictly backwards and
 // ends in a literal.  The range is cut into segments of at most kSeg0
 // bytes; each warp resolves its segments depth first with a stack in
