@@ -170,22 +170,65 @@ __global__ void __launch_bounds__(kThreads, 3) k_wave0(const uint4 *__restrict__
 
 // ------------------------------------------------ persistent schedule
 
+// Exact same-wave dependencies inside one window of triplets (one per
+// lane): bit j of the result is set when this lane's source overlaps the
+// output of lane j < this lane.  Only matches of one block can depend on
+// each other within a wave (a source in another block was final a wave
+// earlier), so lanes whose source does not end in their own block skip the
+// test.
+template <int G>
+__device__ __forceinline__ unsigned same_wave_deps(const Group<G> &g, bool v, uint64_t d, uint64_t sr,
+                                                   uint32_t len, uint32_t log2bs) {
+    const uint64_t blk = d >> log2bs;
+    const bool local = v && ((sr + len - 1) >> log2bs) == blk;
+    unsigned m = 0;
+    if (!g.ballot(local)) return 0u;
+    for (int j = 0; j < G; j++) {
+        const uint64_t dj = g.shfl(d, j);
+        const uint32_t nj = g.shfl(len, j);
+        if (local && j < g.lane && nj && (dj >> log2bs) == blk && sr < dj + nj && dj < sr + len) m |= 1u << j;
+    }
+    return m;
+}
+
+// One look, without waiting, at whether every block of [sr, sr + len) has
+// finished its waves below w (w <= 64, at most 4 blocks); acquire loads.
+__device__ __forceinline__ bool waves_below_now(const unsigned long long *done, uint32_t ww, uint64_t sr,
+                                                uint32_t len, uint32_t w, uint32_t log2bs) {
+    if (w > 64) return false;
+    const uint64_t b0 = sr >> log2bs, b1 = (sr + len - 1) >> log2bs;
+    if (b1 - b0 > 3) return false;
+    const unsigned long long want = w >= 64 ? ~0ULL : ((1ULL << w) - 1ULL);
+    for (uint64_t bb = b0; bb <= b1; bb++)
+        if ((ld_acquire64(done + bb * ww) & want) != want) return false;
+    return true;
+}
+
 // Waves >= 1 in one cooperative launch, by ranges: range r holds the
-// consecutive segments [s0, s1) of one wave (blocks in order).  Each match
+// consecutive triplets [first, next range's first) of one wave.  Each match
 // waits (bounded) until every block its source touches has finished its
-// waves below w (per-block done bits; empty waves are preset), the range
-// copies all its matches together (only matches reading an earlier match
-// of the same block in the same pass are serialised), then sets bit w of
-// each of its blocks.  Ranges wait only for ranges of lower waves, earlier
-// in the list; all groups are co-resident and take their ranges in
-// increasing order (r, r + K, r + 2K, ...), so every wait ends.  STAGED: matches of at least kTmaMin bytes go through the group's
-// shared-memory stage by TMA bulk copies; otherwise all copies go through
-// registers and the kernel runs at higher occupancy.
+// waves below w (per-block done bits; empty waves are preset); the range
+// copies its matches window by window, in dependency levels within a
+// window (a match that reads another's output of the same wave goes after
+// it); then it marks bit w of each block it finished.  A segment (one
+// block's matches of one wave) cut into several ranges is finished by the
+// last of its ranges to end, found with a per-segment counter.  Ranges
+// wait only for ranges of lower waves, earlier in the list; all groups are
+// co-resident and take their ranges in increasing order (r, r + K, r + 2K,
+// ...), so every wait ends.
+// STAGED: matches of at least kTmaMin bytes go through the group's
+// shared-memory stage by TMA bulk copies, and a group looks at its next
+// range before releasing the current one: when that range's sources are
+// already final, its first fill is issued at once, so the bulk copy runs
+// while the current range's stores drain and its blocks are released.
+// Otherwise all copies go through registers and the kernel runs at higher
+// occupancy.
 template <int G, bool STAGED>
-__global__ void __launch_bounds__(kThreads, STAGED ? 1 : 3)
+__global__ void __launch_bounds__(kThreads, STAGED ? 2 : 3)
     k_ranges(const uint4 *__restrict__ ranges, uint64_t n_ranges, const uint4 *__restrict__ seg,
-             unsigned long long *done, uint32_t ww, const uint4 *__restrict__ tri, uint8_t *out,
-             uint32_t log2bs, uint32_t stage_bytes, uint32_t *err, uint32_t spin_limit) {
+             const uint32_t *__restrict__ pieces, uint32_t *seg_cnt, unsigned long long *done, uint32_t ww,
+             const uint4 *__restrict__ tri, uint8_t *out, uint32_t log2bs, uint32_t stage_bytes, uint32_t *err,
+             uint32_t spin_limit) {
     extern __shared__ __align__(128) uint8_t smem[];
     Group<G> g;
     constexpr int kGroups = kThreads / G;
@@ -204,66 +247,113 @@ __global__ void __launch_bounds__(kThreads, STAGED ? 1 : 3)
     }
     const uint64_t gid = (blockIdx.x * (uint64_t)kThreads + threadIdx.x) / G;
     const uint64_t ng = (uint64_t)gridDim.x * kGroups;
+    const uint4 z4 = make_uint4(0, 0, 0, 0);
     bool ok = true;
-    // ranges[n_ranges] is a sentinel: the end of range r is ranges[r + 1].w
-    uint4 rn = gid < n_ranges ? __ldg(ranges + gid) : make_uint4(0, 0, 0, 0);
-    uint32_t tn = gid < n_ranges ? __ldg(ranges + gid + 1).w : 0u;
+    // ranges[n_ranges] is a sentinel: the end of range r is ranges[r + 1].w.
+    // Loaded ahead: the descriptor and first window of this group's next
+    // range (rn, tn, nt2) and the descriptor of the one after (rn3, tn3).
+    auto desc = [&](uint64_t k, uint4 &rd, uint32_t &te) {
+        rd = k < n_ranges ? __ldg(ranges + k) : z4;
+        te = k < n_ranges ? __ldg(ranges + k + 1).w : 0u;
+    };
+    uint4 rc, rn, rn3;
+    uint32_t tc, tn, tn3;
+    desc(gid, rc, tc);
+    desc(gid + ng, rn, tn);
+    uint4 nt = rc.w + g.lane < tc ? __ldg(tri + rc.w + g.lane) : z4;
+    uint4 nt2 = rn.w + g.lane < tn ? __ldg(tri + rn.w + g.lane) : z4;
+    Fill pre = {0, 0, 0, 0};
+    bool pre_on = false;  // the first batch of range `it` has its first fill in flight
     for (uint64_t it = gid; it < n_ranges; it += ng) {
-        const uint4 r = rn;
-        const uint64_t t_begin = r.w, t_end = tn;
-        if (it + ng < n_ranges) {  // next range's descriptor, loaded early
-            rn = __ldg(ranges + it + ng);
-            tn = __ldg(ranges + it + ng + 1).w;
-        }
+        const uint4 r = rc;
+        const uint64_t t_begin = r.w, t_end = tc;
+        desc(it + 2 * ng, rn3, tn3);
         const uint32_t w = r.x, s0 = r.y, s1 = r.z;
-        uint4 nt = t_begin + g.lane < t_end ? __ldg(tri + t_begin + g.lane) : make_uint4(0, 0, 0, 0);
+        const bool has_next = it + ng < n_ranges;
         for (uint64_t cur = t_begin; cur < t_end; cur += G) {
-            const uint64_t i = cur + g.lane;
-            const bool v = i < t_end;
-            const uint4 t = v ? nt : make_uint4(0, 0, 0, 0);
-            if (cur + G + g.lane < t_end) nt = __ldg(tri + cur + G + g.lane);
+            const bool v = cur + g.lane < t_end;
+            const uint4 t = v ? nt : z4;
+            if (cur + G < t_end) nt = cur + G + g.lane < t_end ? __ldg(tri + cur + G + g.lane) : z4;
             const uint64_t d = tri_dst(t), sr = tri_src(t);
             const uint32_t len = v ? tri_len(t) : 0u;
-            const uint64_t blk = d >> log2bs;
-            // every block the source touches (its own included) has finished
-            // its waves below w
-            if (v) {
-                const uint64_t b0 = sr >> log2bs, b1 = (sr + len - 1) >> log2bs;
-                for (uint64_t bb = b0; bb <= b1; bb++)
-                    if (!wait_waves_below(done + bb * ww, w, err, spin_limit)) ok = false;
+            const bool ahead = pre_on && cur == t_begin;
+            if (!ahead) {
+                // every block the source touches (its own included) has
+                // finished its waves below w
+                if (v) {
+                    const uint64_t b0 = sr >> log2bs, b1 = (sr + len - 1) >> log2bs;
+                    for (uint64_t bb = b0; bb <= b1; bb++)
+                        if (!wait_waves_below(done + bb * ww, w, err, spin_limit)) ok = false;
+                }
+                g.sync();
             }
-            g.sync();
-            // segment starts inside this window (block changes)
-            uint64_t pblk = g.shfl_up(blk, 1);
-            if (g.lane == 0) pblk = ~0ULL;
-            const unsigned S = g.ballot(v && blk != pblk);
+            const unsigned deps = same_wave_deps<G>(g, v, d, sr, len, log2bs);
             unsigned rem = g.ballot(v);
+            bool issued = ahead;
             while (rem) {
-                if (STAGED) fence_proxy_async_global();
-                const int f = __ffs(rem) - 1;
-                const unsigned upto = (g.lane == G - 1) ? 0xffffffffu : ((2u << g.lane) - 1u);
-                const unsigned sm = (S | (1u << f)) & ~((1u << f) - 1u) & upto;
-                const int fs = sm ? 31 - __clz(sm) : f;
-                const uint64_t fsd = g.shfl(d, fs);
-                const bool dep = ((rem >> g.lane) & 1u) && g.lane > fs && (sr + len > fsd);
-                const unsigned dmask = g.ballot(dep);
-                const unsigned lim = dmask & (0u - dmask);
-                const unsigned batch = lim ? (rem & (lim - 1u)) : rem;
+                const unsigned batch = g.ballot(((rem >> g.lane) & 1u) && (deps & rem) == 0u);
                 const bool mine = (batch >> g.lane) & 1u;
                 if (STAGED) {
-                    if (!hybrid_copy<G>(g, st, out, d, out + sr, mine ? len : 0u, kTmaMin, piece, err)) ok = false;
+                    if (!issued) fence_proxy_async_global();
+                    const bool longj = mine && len >= kTmaMin;
+                    group_copy<G, 2>(g, out, d, out + sr, (mine && !longj) ? len : 0u);
+                    if (issued || g.ballot(longj)) {
+                        if (!staged_copy_fills<G>(g, st, out, d, out + sr, longj ? len : 0u, piece, pre, issued,
+                                                  err))
+                            return;  // a bulk copy did not complete: no further copies into the stage
+                    }
                 } else {
                     group_copy<G, kUnrollCopy>(g, out, d, out + sr, mine ? len : 0u);
                 }
                 g.sync();
                 rem &= ~batch;
+                issued = false;
             }
         }
+        pre_on = false;
+        // a look at the next range of this group: when the sources of its
+        // first window are final already, its first fill is issued now, so
+        // the bulk copy runs while this range's stores drain and its blocks
+        // are released
+        if (STAGED && has_next && g.ballot(!ok) == 0u) {
+            const bool v2 = rn.w + g.lane < tn;
+            const uint64_t d2 = tri_dst(nt2), s2 = tri_src(nt2);
+            const uint32_t n2 = v2 ? tri_len(nt2) : 0u;
+            const bool ready = !v2 || waves_below_now(done, ww, s2, n2, rn.x, log2bs);
+            if (g.ballot(!ready) == 0u) {
+                const unsigned deps2 = same_wave_deps<G>(g, v2, d2, s2, n2, log2bs);
+                const unsigned all2 = g.ballot(v2);
+                const bool long2 = v2 && n2 >= kTmaMin && (deps2 & all2) == 0u;
+                if (g.ballot(long2)) {
+                    fence_proxy_async_global();
+                    pre.done = 0;
+                    fill_issue<G>(g, st, out + s2, long2 ? n2 : 0u, piece, pre);
+                    pre_on = true;
+                }
+            }
+        }
+        // release: this range's writes, then bit w of every block it
+        // finished (of a shared segment, only the last range to end)
         __threadfence();
         g.sync();
         const unsigned long long bit = 1ULL << (w % 64);
-        for (uint32_t k = s0 + g.lane; k < s1; k += G)
-            atomicOr(done + (uint64_t)__ldg(seg + k).x * ww + w / 64, bit);
+        for (uint32_t k = s0 + g.lane; k < s1; k += G) {
+            const uint64_t word = (uint64_t)__ldg(seg + k).x * ww + w / 64;
+            const uint32_t pc = __ldg(pieces + k);
+            if (pc > 1) {
+                if (atomicAdd(seg_cnt + k, 1u) != pc - 1) continue;
+                seg_cnt[k] = 0;  // the last range of the segment resets the count for the next decode
+                __threadfence();
+            }
+            atomicOr(done + word, bit);
+        }
+        // shift the loaded-ahead state by one range
+        nt = nt2;
+        rc = rn;
+        tc = tn;
+        rn = rn3;
+        tn = tn3;
+        nt2 = rn.w + g.lane < tn ? __ldg(tri + rn.w + g.lane) : z4;
     }
     if (!ok) atomicOr(err, kErrTimeout);
 }
@@ -339,7 +429,7 @@ int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st, cudaEvent_t phas
     constexpr int gpc = kThreads / G;  // groups per CTA
     const unsigned grid0 = (h->n_blocks + gpc - 1) / gpc;
     k_wave0<G><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
-                                            h->d_blk_lit, h->d_slot, h->flat ? nullptr : (uint4 *)h->d_tri, out,
+                                            h->d_blk_lit, h->d_slot, nullptr, out,
                                             h->n_blocks, h->log2_bs, nullptr, nullptr, 0);
     if (phase) cudaEventRecord(phase, st);
     constexpr int ITEMS = 2;
@@ -389,7 +479,7 @@ int launch_persistent(aclz_handle *h, uint8_t *out, uint32_t ctas_per_sm, cudaSt
     constexpr int gpc = kThreads / G;
     const unsigned grid0 = (h->n_blocks + gpc - 1) / gpc;
     k_wave0<G><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
-                                            h->d_blk_lit, h->d_slot, h->flat ? nullptr : (uint4 *)h->d_tri, out,
+                                            h->d_blk_lit, h->d_slot, nullptr, out,
                                             h->n_blocks, h->log2_bs, h->d_pending, h->d_done,
                                             h->n_wave_words);
     if (phase) cudaEventRecord(phase, st);
@@ -447,6 +537,8 @@ int launch_persistent(aclz_handle *h, uint8_t *out, uint32_t ctas_per_sm, cudaSt
     const uint4 *ranges = (const uint4 *)h->d_ranges;
     uint64_t n_ranges = h->n_ranges;
     const uint4 *seg = (const uint4 *)h->d_seg;
+    const uint32_t *pieces = h->d_seg_pieces;
+    uint32_t *seg_cnt = h->d_seg_cnt;
     unsigned long long *done = (unsigned long long *)h->d_done;
     uint32_t ww = h->n_wave_words;
     const uint4 *tri = (const uint4 *)h->d_tri;
@@ -455,7 +547,7 @@ int launch_persistent(aclz_handle *h, uint8_t *out, uint32_t ctas_per_sm, cudaSt
     uint32_t *err = h->d_err;
     uint32_t spin_limit =
         (uint32_t)std::min<uint64_t>(kSpinLimitMax, (uint64_t)kSpinLimitMin * std::max<uint32_t>(1u, h->n_waves / 256));
-    void *args[] = {&ranges, &n_ranges, &seg, &done, &ww, &tri, &out, &log2bs, &sb, &err, &spin_limit};
+    void *args[] = {&ranges, &n_ranges, &seg, &pieces, &seg_cnt, &done, &ww, &tri, &out, &log2bs, &sb, &err, &spin_limit};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kThreads), args, o.smem, st);
     if (e == cudaErrorCooperativeLaunchTooLarge && o.per_sm > 1) {
         // fewer co-resident CTAs than the occupancy estimate: one per SM
@@ -596,7 +688,9 @@ extern "C" int aclz_device_status(aclz_handle *h, void *stream) {
     if (cudaMemcpyAsync(&e, h->d_err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return ACLZ_E_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return ACLZ_E_CUDA;
     if (e) {
+        // a failed persistent decode may leave segment counts mid-way
         cudaMemsetAsync(h->d_err, 0, 4, st);
+        if (h->d_seg_cnt) cudaMemsetAsync(h->d_seg_cnt, 0, 4 * h->n_seg, st);
         cudaStreamSynchronize(st);
     }
     if (e & kErrTimeout) return ACLZ_E_TIMEOUT;

@@ -357,18 +357,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
 constexpr uint32_t kMbarSpinLimit = 1u << 26;
 
 // Wait for the stage's current phase (bounded; sets kErrTimeout on err).
+// A false return means the bulk copy may still be writing the stage: the
+// caller must issue no further copies into it and end the launch.
 __device__ __forceinline__ bool stage_wait(Stage &st, uint32_t *err) {
     uint32_t spins = 0;
-    bool ok = true;
     while (!mbar_try_wait(st.bar, st.phase)) {
         if (++spins > kMbarSpinLimit) {
             atomicOr(err, kErrTimeout);
-            ok = false;
-            break;
+            return false;
         }
     }
     st.phase ^= 1u;
-    return ok;
+    return true;
 }
 
 // Realign-and-store of one staged job: output [d, d + n) from the shared
@@ -410,61 +410,82 @@ __device__ __forceinline__ void store_staged_job(const Group<G> &g, uint8_t *out
     }
 }
 
-// Copy jobs through shared memory: every lane's job (d, s, n) is cut into
-// pieces of at most `piece` bytes; the aligned source span of each piece
-// is fetched by one bulk copy into the stage (packed in lane order, as
-// many as fit), then the group realigns the bytes from shared memory and
-// writes aligned 16-byte words to the output, one job at a time.  The
-// caller has made the source bytes final and visible to bulk copies
-// (fence_proxy_async_global after acquiring them).  Jobs must be
-// independent.
+// One fill of a group's stage, split in two steps so that a fill can be
+// issued ahead (while the group finishes other work) and consumed later.
+// Per lane: done = bytes of its job written by earlier fills, off = stage
+// offset of its aligned source span in the fill in flight, len = bytes of
+// its piece in that fill (0: none), head = offset of the piece's first byte
+// within the span.
+struct Fill {
+    uint32_t done, off, len, head;
+};
+
+// Issue one fill for every lane's job (s, n) from f.done on: pieces of at
+// most `piece` bytes packed in lane order while they fit, one bulk copy per
+// piece.  Returns false, issuing nothing, when no lane has bytes left.  The
+// caller has made the sources final and visible to bulk copies.
 template <int G>
-__device__ __forceinline__ bool staged_copy(const Group<G> &g, Stage &st, uint8_t *out, uint64_t d,
-                                            const uint8_t *s, uint32_t n, uint32_t piece, uint32_t *err) {
-    bool ok = true;
-    uint32_t done = 0;
-    for (;;) {
-        const uint32_t rem = n - done;
-        if (!g.ballot(rem > 0)) break;
-        const uint32_t len = rem < piece ? rem : piece;
-        const uintptr_t ps = reinterpret_cast<uintptr_t>(s) + done;
-        const uintptr_t sa = ps & ~(uintptr_t)15;
-        const uint32_t span = rem ? (uint32_t)(((ps + len + 15) & ~(uintptr_t)15) - sa) : 0u;
-        const uint32_t incl = g.scan_incl(span);
-        const bool take = rem > 0 && incl <= st.bytes;
-        const unsigned tm = g.ballot(take);
-        const int last = 31 - __clz(tm);
-        const uint32_t tx = g.shfl(incl, last);
-        if (g.lane == 0) mbar_expect_tx(st.bar, tx);
-        g.sync();
-        const uint32_t off = incl - span;
-        if (take) tma_load_1d(st.buf + off, reinterpret_cast<const void *>(sa), span, st.bar);
-        if (!stage_wait(st, err)) ok = false;
-        const uint8_t *src = st.buf + off + (uint32_t)(ps - sa);
-        for (unsigned m = tm; m; m &= m - 1) {
-            const int j = __ffs(m) - 1;
-            const uint64_t dj = g.shfl(d + done, j);
-            const uint8_t *sj =
-                reinterpret_cast<const uint8_t *>(g.shfl(reinterpret_cast<unsigned long long>(src), j));
-            const uint32_t nj = g.shfl(len, j);
-            store_staged_job<G>(g, out, dj, sj, nj);
-        }
-        g.sync();
-        fence_proxy_async_shared();
-        if (take) done += len;
+__device__ __forceinline__ bool fill_issue(const Group<G> &g, Stage &st, const uint8_t *s, uint32_t n,
+                                           uint32_t piece, Fill &f) {
+    const uint32_t rem = n - f.done;
+    f.len = 0;
+    if (!g.ballot(rem > 0)) return false;
+    const uint32_t len = rem < piece ? rem : piece;
+    const uintptr_t ps = reinterpret_cast<uintptr_t>(s) + f.done;
+    const uintptr_t sa = ps & ~(uintptr_t)15;
+    const uint32_t span = rem ? (uint32_t)(((ps + len + 15) & ~(uintptr_t)15) - sa) : 0u;
+    const uint32_t incl = g.scan_incl(span);
+    const bool take = rem > 0 && incl <= st.bytes;
+    const unsigned tm = g.ballot(take);
+    const uint32_t tx = g.shfl(incl, 31 - __clz(tm));
+    if (g.lane == 0) mbar_expect_tx(st.bar, tx);
+    g.sync();
+    f.off = incl - span;
+    f.head = (uint32_t)(ps - sa);
+    if (take) {
+        tma_load_1d(st.buf + f.off, reinterpret_cast<const void *>(sa), span, st.bar);
+        f.len = len;
     }
-    return ok;
+    return true;
 }
 
-// Short jobs through registers, long ones through the stage.
+// Wait for the fill in flight and write its pieces to out[d + done, ...),
+// one job after another (store_staged_job).  False, on every lane of the
+// group, when a lane's wait timed out (see stage_wait).
 template <int G>
-__device__ __forceinline__ bool hybrid_copy(const Group<G> &g, Stage &st, uint8_t *out, uint64_t d,
-                                            const uint8_t *s, uint32_t n, uint32_t tma_min, uint32_t piece,
-                                            uint32_t *err) {
-    const bool longj = n >= tma_min;
-    group_copy<G, 2>(g, out, d, s, longj ? 0u : n);
-    if (!g.ballot(longj)) return true;
-    return staged_copy<G>(g, st, out, d, s, longj ? n : 0u, piece, err);
+__device__ __forceinline__ bool fill_consume(const Group<G> &g, Stage &st, uint8_t *out, uint64_t d, Fill &f,
+                                             uint32_t *err) {
+    const bool waited = stage_wait(st, err);
+    if (g.ballot(!waited)) return false;
+    const uint8_t *src = st.buf + f.off + f.head;
+    for (unsigned m = g.ballot(f.len > 0); m; m &= m - 1) {
+        const int j = __ffs(m) - 1;
+        const uint64_t dj = g.shfl(d + f.done, j);
+        const uint8_t *sj = reinterpret_cast<const uint8_t *>(g.shfl(reinterpret_cast<unsigned long long>(src), j));
+        const uint32_t nj = g.shfl(f.len, j);
+        store_staged_job<G>(g, out, dj, sj, nj);
+    }
+    g.sync();
+    fence_proxy_async_shared();
+    f.done += f.len;
+    f.len = 0;
+    return true;
+}
+
+// Staged copy of every lane's job (d, s, n) through fills; `issued` says
+// that the first fill of these jobs (f.done = 0) is already in flight.
+template <int G>
+__device__ __forceinline__ bool staged_copy_fills(const Group<G> &g, Stage &st, uint8_t *out, uint64_t d,
+                                                  const uint8_t *s, uint32_t n, uint32_t piece, Fill &f,
+                                                  bool issued, uint32_t *err) {
+    if (!issued) {
+        f.done = 0;
+        if (!fill_issue<G>(g, st, s, n, piece, f)) return true;
+    }
+    for (;;) {
+        if (!fill_consume<G>(g, st, out, d, f, err)) return false;
+        if (!fill_issue<G>(g, st, s, n, piece, f)) return true;
+    }
 }
 
 }  // namespace aclz

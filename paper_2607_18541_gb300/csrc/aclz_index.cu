@@ -12,6 +12,7 @@
 //     k_tags_check   legality of tags supplied by the container.
 //  3. k_wave_hist, an exclusive scan and k_slots: the wave-major, block-
 //     ordered worklist slot of every deferred match.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -370,6 +371,27 @@ __global__ void __launch_bounds__(256) k_slots(const uint4 *__restrict__ tok,
     }
 }
 
+// Triplets of the deferred matches, written once at upload: tri[slot[i]]
+// = (dst, src, len) of deferred match token i, so the worklists are in
+// wave-major, block order and in token order within a block.
+__global__ void __launch_bounds__(256) k_tri_build(const uint4 *__restrict__ tok,
+                                                   const uint64_t *__restrict__ blk_tok,
+                                                   const uint32_t *__restrict__ tokdst,
+                                                   const uint32_t *__restrict__ slot, uint32_t nb,
+                                                   uint32_t log2bs, uint4 *__restrict__ tri) {
+    const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;
+    const uint64_t bstart = (uint64_t)b << log2bs;
+    for (uint64_t i = blk_tok[b] + lane; i < blk_tok[b + 1]; i += 32) {
+        const uint32_t sl = __ldg(slot + i);
+        if (sl == 0xffffffffu) continue;
+        const uint4 t = __ldg(tok + i);
+        const uint64_t dm = bstart + __ldg(tokdst + i) + t.x;
+        tri[sl] = make_uint4((uint32_t)dm, (uint32_t)(dm >> 32), t.z, (t.w & 0xffu) | (t.y << 8));
+    }
+}
+
 // flag[k] = 1 when (wave, block) segment k is non-empty; base is the
 // exclusive scan of the segment counts, *total its sum
 __global__ void k_seg_flags(const uint32_t *base, uint64_t M, const uint32_t *total, uint32_t *flag) {
@@ -407,42 +429,106 @@ __global__ void k_segs_build(const uint32_t *base, const uint32_t *pos, const ui
     for (uint32_t k2 = wk + 1; k2 < ww; k2++) pending[(uint64_t)b * ww + k2] = 0;
 }
 
-// A range starts at segment s when s begins a wave or its first triplet
-// falls in a new multiple of T.
-__global__ void k_range_flags(const uint4 *seg, uint64_t n, uint32_t T, uint32_t *flag) {
-    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
+// seg_of[t] = the segment holding triplet t (segments are consecutive
+// runs of the triplet array).
+__global__ void k_seg_of(const uint4 *__restrict__ seg, uint64_t nseg, uint32_t *__restrict__ seg_of) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < nseg;
          s += (uint64_t)gridDim.x * blockDim.x) {
         const uint4 a = seg[s];
-        bool f = s == 0;
-        if (!f) {
-            const uint4 p = seg[s - 1];
-            f = a.y != p.y || (a.z / T) != (p.z / T);
-        }
-        flag[s] = f ? 1u : 0u;
+        for (uint32_t k = 0; k < a.w; k++) seg_of[a.z + k] = (uint32_t)s;
     }
 }
 
-// ex is the exclusive scan of the range-start flags, nr their sum:
-// segment s starts range ex[s] when ex[s + 1] > ex[s].  ranges[r] =
-// {wave, first segment, end segment, first triplet}; ranges[nr] is a
-// sentinel whose first triplet is the end of the last range.
-__global__ void k_range_build(const uint4 *seg, const uint32_t *ex, uint64_t n, uint32_t nr,
-                              uint32_t n_tri, uint4 *ranges) {
-    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
+// segdep[s] = 1 when a match of segment s reads bytes that an earlier
+// match of the same segment writes (a chain inside one block and wave):
+// such a segment is never cut between two ranges.  The outputs of one
+// segment are disjoint and in increasing order, so the last earlier output
+// starting below the source's end decides.
+__global__ void k_seg_dep(const uint4 *__restrict__ tri, const uint4 *__restrict__ seg,
+                          const uint32_t *__restrict__ seg_of, uint64_t n, uint32_t *segdep) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = seg_of[t];
+        const uint64_t a = seg[s].z;
+        if (t == a) continue;
+        const uint4 x = tri[t];
+        const uint64_t src = (uint64_t)x.z | ((uint64_t)(x.w & 0xffu) << 32);
+        const uint64_t se = src + (x.w >> 8);
+        uint64_t lo = a, hi = t;  // first j in [a, t) with dst_j >= se
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) >> 1;
+            const uint4 y = tri[mid];
+            const uint64_t dj = (uint64_t)y.x | ((uint64_t)(y.y & 0xffu) << 32);
+            if (dj < se) lo = mid + 1; else hi = mid;
+        }
+        if (lo > a) {
+            const uint4 y = tri[lo - 1];
+            const uint64_t dj = (uint64_t)y.x | ((uint64_t)(y.y & 0xffu) << 32);
+            if (dj + (y.w >> 8) > src) segdep[s] = 1u;
+        }
+    }
+}
+
+// Range starts.  In wave w (triplets from wstart[w]) a range starts every
+// wT[w] triplets, except inside a segment with an internal chain, whose
+// candidate starts move to the end of that segment.
+__global__ void k_range_flags(const uint4 *__restrict__ seg, const uint32_t *__restrict__ seg_of,
+                              const uint32_t *__restrict__ segdep, const uint64_t *__restrict__ wstart,
+                              const uint32_t *__restrict__ wT, uint64_t n, uint32_t *flag) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = seg_of[t];
+        const uint4 a = seg[s];
+        const uint64_t ws = wstart[a.y];
+        const uint64_t T = wT[a.y];
+        bool f;
+        if (t == ws) {
+            f = true;
+        } else if (segdep[s] && t > a.z) {
+            f = false;
+        } else if ((t - ws) % T == 0) {
+            f = true;
+        } else if (t == a.z && s > 0) {
+            const uint4 p = seg[s - 1];
+            f = p.y == a.y && segdep[s - 1] && (t - 1 - ws) / T > (p.z - ws) / T;
+        } else {
+            f = false;
+        }
+        flag[t] = f ? 1u : 0u;
+    }
+}
+
+// ranges[r] = {wave, first segment, end segment, first triplet} from the
+// exclusive scan ex of the range-start flags (nr ranges); ranges[nr] is a
+// sentinel whose first triplet is n.
+__global__ void k_range_build(const uint4 *__restrict__ seg, const uint32_t *__restrict__ seg_of,
+                              const uint32_t *__restrict__ flag, const uint32_t *__restrict__ ex, uint64_t n,
+                              uint32_t nr, uint4 *ranges) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        if (flag[t]) {
+            const uint32_t r = ex[t];
+            const uint32_t s = seg_of[t];
+            ranges[r].x = seg[s].y;
+            ranges[r].y = s;
+            ranges[r].w = (uint32_t)t;
+            if (r > 0) ranges[r - 1].z = seg_of[t - 1] + 1;
+        }
+        if (t + 1 == n) {
+            ranges[nr - 1].z = seg_of[t] + 1;
+            ranges[nr] = make_uint4(0u, seg_of[t] + 1, seg_of[t] + 1, (uint32_t)n);
+        }
+    }
+}
+
+// pieces[s] = number of ranges that hold triplets of segment s.
+__global__ void k_seg_pieces(const uint4 *__restrict__ seg, const uint32_t *__restrict__ flag,
+                             const uint32_t *__restrict__ ex, uint64_t nseg, uint32_t *pieces) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < nseg;
          s += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t r = ex[s];
-        const uint32_t nx = s + 1 < n ? ex[s + 1] : nr;
-        if (nx > r) {
-            const uint4 a = seg[s];
-            ranges[r].x = a.y;
-            ranges[r].y = (uint32_t)s;
-            ranges[r].w = a.z;
-            if (r > 0) ranges[r - 1].z = (uint32_t)s;
-        }
-        if (s + 1 == n) {
-            ranges[nr - 1].z = (uint32_t)n;
-            ranges[nr] = make_uint4(0u, (uint32_t)n, (uint32_t)n, n_tri);
-        }
+        const uint4 a = seg[s];
+        const uint64_t f = a.z, l = a.z + a.w - 1;
+        pieces[s] = (ex[l] + flag[l]) - (ex[f] + flag[f]) + 1;
     }
 }
 
@@ -697,7 +783,12 @@ int aclz::build_index(aclz_handle *h, bool has_tags, uint32_t given_waves, bool 
         CK(cudaMemcpyAsync(h->wave_start.data() + 1, starts.p, 8 * (maxtag + 1), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         h->n_deferred = h->wave_start[h->n_waves];
-        if (h->n_deferred) CK(cudaMalloc(&h->d_tri, 16 * h->n_deferred));
+        if (h->n_deferred) {
+            CK(cudaMalloc(&h->d_tri, 16 * h->n_deferred));
+            k_tri_build<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_tokdst, h->d_slot,
+                                                  nb, h->log2_bs, (uint4 *)h->d_tri);
+            CK(cudaGetLastError());
+        }
         h->mean_deferred_len = h->n_deferred ? (double)defb_total / (double)h->n_deferred : 0.0;
         rc = aclz_set_range_bytes(h, h->range_bytes, stream);
         if (rc) { cleanup(); return rc; }
@@ -803,8 +894,9 @@ extern "C" int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, 
 
 extern "C" int aclz_free(aclz_handle *h) {
     if (!h) return ACLZ_E_INVAL;
-    void *ps[] = {h->d_tok, h->d_lit, h->d_blk_tok, h->d_blk_lit, h->d_slot, h->d_tokdst, h->d_toklit,
-                  h->d_tri, h->d_err, h->d_seg, h->d_ranges, h->d_pending, h->d_done};
+    void *ps[] = {h->d_tok, h->d_lit,    h->d_blk_tok, h->d_blk_lit,      h->d_slot,      h->d_tokdst,
+                  h->d_toklit, h->d_tri, h->d_err,     h->d_seg,          h->d_ranges,    h->d_seg_pieces,
+                  h->d_seg_cnt, h->d_pending, h->d_done};
     for (void *p : ps)
         if (p) cudaFree(p);
     delete h;
@@ -849,34 +941,70 @@ extern "C" int aclz_set_range_bytes(aclz_handle *h, uint32_t range_bytes, void *
     cudaStream_t st = (cudaStream_t)stream;
     h->range_bytes = range_bytes;
     h->range_T = range_matches(range_bytes, h->mean_deferred_len);
-    if (h->d_ranges) {
-        cudaFree(h->d_ranges);
-        h->d_ranges = nullptr;
+    for (void **pp : {&h->d_ranges, (void **)&h->d_seg_pieces, (void **)&h->d_seg_cnt}) {
+        if (*pp) cudaFree(*pp);
+        *pp = nullptr;
     }
     h->n_ranges = 0;
-    const uint64_t nseg = h->n_seg;
-    if (!nseg) return ACLZ_OK;
-    uint32_t *rflag = nullptr, *d_nr = nullptr;
-    if (cudaMalloc((void **)&rflag, 4 * (size_t)nseg + 16) != cudaSuccess) return ACLZ_E_NOMEM;
-    d_nr = rflag + nseg;
+    const uint64_t nseg = h->n_seg, n = h->n_deferred;
+    if (!nseg || !n) return ACLZ_OK;
+    // matches per range by wave: range_T in large waves; a small wave is cut
+    // into about kRangesPerSm ranges per SM (down to one match each), so its
+    // matches spread over the resident groups and every dependency hop of
+    // the wavefront costs the latency of a short range, not of a long one
+    int dev_sms = 0;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device);
+    const uint64_t P = (uint64_t)std::max(1, dev_sms) * kRangesPerSm;
+    const uint32_t nw = h->n_waves;
+    std::vector<uint32_t> wT(nw, 1u);
+    for (uint32_t w = 1; w < nw; w++) {
+        const uint64_t nwv = h->wave_start[w + 1] - h->wave_start[w];
+        wT[w] = (uint32_t)std::min<uint64_t>(h->range_T, std::max<uint64_t>(1, (nwv + P - 1) / P));
+    }
+    DevBuf b_of, b_dep, b_flag, b_ex, b_ws, b_wT;
     int rc = ACLZ_OK;
-    k_range_flags<<<1024, 256, 0, st>>>((const uint4 *)h->d_seg, nseg, h->range_T, rflag);
-    rc = device_excl_scan(rflag, nseg, d_nr, st);
+    auto ck = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == ACLZ_OK) {
+            note_cuda_error(e);
+            rc = e == cudaErrorMemoryAllocation ? ACLZ_E_NOMEM : ACLZ_E_CUDA;
+        }
+        return rc == ACLZ_OK;
+    };
+    if (!ck(cudaMalloc(&b_of.p, 4 * n)) || !ck(cudaMalloc(&b_dep.p, 4 * nseg)) ||
+        !ck(cudaMalloc(&b_flag.p, 4 * n)) || !ck(cudaMalloc(&b_ex.p, 4 * n + 16)) ||
+        !ck(cudaMalloc(&b_ws.p, 8 * ((size_t)nw + 1))) || !ck(cudaMalloc(&b_wT.p, 4 * (size_t)nw)))
+        return rc;
+    uint32_t *seg_of = (uint32_t *)b_of.p, *segdep = (uint32_t *)b_dep.p, *flag = (uint32_t *)b_flag.p,
+             *ex = (uint32_t *)b_ex.p, *d_nr = ex + n;
+    const uint4 *seg = (const uint4 *)h->d_seg;
+    const unsigned grid = (unsigned)std::min<uint64_t>(4096, (n + 255) / 256);
+    const unsigned gseg = (unsigned)std::min<uint64_t>(4096, (nseg + 255) / 256);
+    ck(cudaMemcpyAsync(b_ws.p, h->wave_start.data(), 8 * ((size_t)nw + 1), cudaMemcpyHostToDevice, st));
+    ck(cudaMemcpyAsync(b_wT.p, wT.data(), 4 * (size_t)nw, cudaMemcpyHostToDevice, st));
+    ck(cudaMemsetAsync(segdep, 0, 4 * nseg, st));
+    if (rc) return rc;
+    k_seg_of<<<gseg, 256, 0, st>>>(seg, nseg, seg_of);
+    k_seg_dep<<<grid, 256, 0, st>>>((const uint4 *)h->d_tri, seg, seg_of, n, segdep);
+    k_range_flags<<<grid, 256, 0, st>>>(seg, seg_of, segdep, (const uint64_t *)b_ws.p, (const uint32_t *)b_wT.p, n,
+                                         flag);
+    ck(cudaGetLastError());
+    ck(cudaMemcpyAsync(ex, flag, 4 * n, cudaMemcpyDeviceToDevice, st));
+    if (rc) return rc;
+    rc = device_excl_scan(ex, n, d_nr, st);
     uint32_t nr = 0;
-    if (rc == ACLZ_OK && cudaMemcpyAsync(&nr, d_nr, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = ACLZ_E_CUDA;
-    if (rc == ACLZ_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = ACLZ_E_CUDA;
+    if (rc == ACLZ_OK) ck(cudaMemcpyAsync(&nr, d_nr, 4, cudaMemcpyDeviceToHost, st));
+    if (rc == ACLZ_OK) ck(cudaStreamSynchronize(st));
     if (rc == ACLZ_OK && nr) {
-        if (cudaMalloc(&h->d_ranges, 16 * ((size_t)nr + 1)) != cudaSuccess) {
-            rc = ACLZ_E_NOMEM;
-        } else {
-            h->n_ranges = nr;
-            k_range_build<<<1024, 256, 0, st>>>((const uint4 *)h->d_seg, rflag, nseg, nr,
-                                                 (uint32_t)h->n_deferred, (uint4 *)h->d_ranges);
-            if (cudaGetLastError() != cudaSuccess) rc = ACLZ_E_CUDA;
-            if (cudaStreamSynchronize(st) != cudaSuccess) rc = ACLZ_E_CUDA;
+        if (ck(cudaMalloc(&h->d_ranges, 16 * ((size_t)nr + 1))) && ck(cudaMalloc((void **)&h->d_seg_pieces, 4 * nseg)) &&
+            ck(cudaMalloc((void **)&h->d_seg_cnt, 4 * nseg))) {
+            k_range_build<<<grid, 256, 0, st>>>(seg, seg_of, flag, ex, n, nr, (uint4 *)h->d_ranges);
+            k_seg_pieces<<<gseg, 256, 0, st>>>(seg, flag, ex, nseg, h->d_seg_pieces);
+            ck(cudaGetLastError());
+            ck(cudaMemsetAsync(h->d_seg_cnt, 0, 4 * nseg, st));
+            ck(cudaStreamSynchronize(st));
+            if (rc == ACLZ_OK) h->n_ranges = nr;
         }
     }
-    cudaFree(rflag);
     return rc;
 }
 

@@ -76,6 +76,9 @@ int build_index(aclz_handle *h, bool has_tags, uint32_t given_waves, bool flat_l
 using FillFn = int (*)(aclz_handle *h, const View &v, const void *ctx, void *stream);
 int upload_view(const View &v, uint32_t flags, void *stream, FillFn fill, const void *ctx, aclz_handle **out);
 
+// Ranges per SM a small wave is cut into (about one per resident group).
+constexpr uint32_t kRangesPerSm = 16;
+
 // Matches per work range for a target byte size of deferred matches.
 inline uint32_t range_matches(uint32_t range_bytes, double mean_len) {
     double t = mean_len > 0 ? (double)range_bytes / mean_len : 16.0;
@@ -101,19 +104,24 @@ struct aclz_handle {
     uint32_t *d_slot = nullptr;   // per token: triplet slot of a deferred match, else ~0u
     uint32_t *d_tokdst = nullptr; // per token: block-relative offset of its first byte
     uint32_t *d_toklit = nullptr; // per token: block-relative offset of its first literal
-    void *d_tri = nullptr;        // n_deferred x 16 B triplets (decode scratch)
+    void *d_tri = nullptr;        // n_deferred x 16 B triplets (dst, src, len), built at upload
     uint32_t *d_err = nullptr;    // latched device status bits
     std::vector<uint64_t> wave_start;  // n_waves + 1 entries into the triplet array
     // persistent-mode schedule.  A segment is the run of one block's
     // matches in one wave's worklist: seg[s] = {block, wave, triplet offset,
-    // count}, wave-major then block order.  Items are [0, n_blocks) the
-    // wave-0 block decodes, then the ranges: runs of consecutive segments of
-    // one wave holding about range_T triplets, range[r] = {wave, first
-    // segment, end segment, 0}.
+    // count}, wave-major then block order.  A range is a run of consecutive
+    // triplets of one wave: range[r] = {wave, first segment, end segment,
+    // first triplet}, with a sentinel after the last.  Ranges hold up to
+    // range_T triplets in large waves and fewer in small ones; they may cut
+    // a segment in pieces unless one of its matches reads another's output.
+    // seg_pieces[s] counts the ranges that share segment s, and seg_cnt[s]
+    // counts the finished ones during a decode (reset by the last).
     void *d_seg = nullptr;
     void *d_ranges = nullptr;
+    uint32_t *d_seg_pieces = nullptr;
+    uint32_t *d_seg_cnt = nullptr;
     uint64_t n_seg = 0, n_ranges = 0;
-    uint32_t range_T = 16;         // matches per range (from range_bytes / mean length)
+    uint32_t range_T = 16;         // matches per range in large waves (from range_bytes / mean length)
     uint32_t range_bytes = 4096;
     double mean_deferred_len = 0;  // mean length of the deferred matches
     // per block, n_wave_words 64-bit words: bit w of pending = block has work
@@ -122,7 +130,7 @@ struct aclz_handle {
     uint64_t *d_pending = nullptr;
     uint64_t *d_done = nullptr;
     // set by aclz_flatten: the deferred work items are origin pieces in one
-    // wave, built at flatten time (wave 0 writes no triplets)
+    // wave, built at flatten time
     bool flat = false;
     // set when the (wave, block) tables of the plain schedule would be too
     // large (deep copy chains): the upload then flattens
