@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--G", type=int, default=32)
     ap.add_argument("--mode", default="auto", choices=["auto", "waves", "persistent"])
     ap.add_argument("--ctas-per-sm", type=int, default=2)
-    ap.add_argument("--range-bytes", type=int, default=4096)
+    ap.add_argument("--range-bytes", type=int, default=20480)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

@@ -239,9 +239,15 @@ int aclz_flatten(aclz_handle *h, void *stream);
  * After any other error the handle is left part-way and must be freed. */
 int aclz_reshape(aclz_handle *h, uint32_t rounds, void *stream);
 
-/* Regroup the persistent schedule: consecutive (block, wave) segments are
- * packed into work ranges of about range_bytes of deferred matches (upload
- * picks 4 KiB).  Synchronizes the stream.  Used by the autotuner. */
+/* Regroup the persistent schedule into work ranges: runs of consecutive
+ * deferred matches of one wave (wave-major, block order), of about
+ * range_bytes of matches (at least 8 matches, at most 4096) in large waves;
+ * a wave with fewer matches than about 16 ranges per SM of that size is cut
+ * into that many ranges (down to one match each), so the short dependency
+ * hops at the start and end of the wavefront (Sec. I) run one match per
+ * group.  A range may cut one block's matches of a wave in two, unless one
+ * of them reads another's output.  Upload picks 20 KiB.  Synchronizes the
+ * stream.  Used by the autotuner. */
 int aclz_set_range_bytes(aclz_handle *h, uint32_t range_bytes, void *stream);
 
 typedef struct aclz_decode_cfg {

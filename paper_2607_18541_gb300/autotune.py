@@ -51,7 +51,7 @@ def measure(h: int, out, reps: int = 5, warmup: int = 2, stream=None, **cfg) -> 
 
 
 def tune(build, total: int, block_sizes=(8192, 16384, 32768, 65536, 131072), Gs=(8, 16, 32),
-         ctas=(0, 2), range_bytes=(4096, 8192), top: int = 4, reps: int = 5, stream=None) -> dict:
+         ctas=(0, 2), range_bytes=(8192, 20480), top: int = 4, reps: int = 5, stream=None) -> dict:
     """build(block_size) -> container bytes of the same data at that block
     size; total = the data's bytes (GB/s are total / time).  Returns
     {"best": {...}, "trials": [...]}."""

@@ -122,7 +122,7 @@ struct aclz_handle {
     uint32_t *d_seg_cnt = nullptr;
     uint64_t n_seg = 0, n_ranges = 0;
     uint32_t range_T = 16;         // matches per range in large waves (from range_bytes / mean length)
-    uint32_t range_bytes = 4096;
+    uint32_t range_bytes = 20480;
     double mean_deferred_len = 0;  // mean length of the deferred matches
     // per block, n_wave_words 64-bit words: bit w of pending = block has work
     // in wave w (bit 0 always); done = waves finished (empty waves preset)
