@@ -8,8 +8,13 @@ One JSON line on rank 0.  `value` is device-resident decode throughput
 (container already in HBM); `e2e` is the same metric through the public C
 ABI from pinned host buffers, the upload (host->device copy and index
 build) and the read-back of the decoded bytes inside the timed region.
-`--impl reference` times the CPU oracle's sequential decoder instead, on a
-bounded sample of the same workload.
+Beside the headline (at one GPU): `sweep`, the same recipe at the other
+match lengths of Table II; `seek`, p50/p99 latency and GB/s of region seeks
+served from a compressed word-text corpus held in HBM (the metric's second
+half); `cpu_baseline`, the CPU oracle's sequential decoder on this same
+workload.  `--impl reference` times that oracle decoder as the reference
+arm (the same workload, or a bounded sample of it when K steps would take
+over about two minutes).
 
 Multi-GPU: the decode does not shard (absolute sources reach anywhere
 earlier), so N ranks run N independent replicas (weak scaling, no
@@ -51,6 +56,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--sweep", default="32,64,128,256,512",
+                    help="match lengths of the sweep block (same recipe; empty string: none)")
+    ap.add_argument("--sweep-steps", type=int, default=20)
+    ap.add_argument("--seek-gib", type=float, default=8.0,
+                    help="serving corpus size for the seek block (0: no seek block)")
+    ap.add_argument("--seek-requests", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -100,6 +111,23 @@ def phase_bytes(sw, tags):
     dbytes = int(ml[deferred].sum())
     w0 = 16 * sw.n_tokens + 2 * int(sw.literals.size) + 2 * (int(ml.sum()) - dbytes)
     return w0, 2 * dbytes, int(deferred.sum())
+
+
+RATED_HBM_GBS = 7900.0  # GB300 HBM3e nominal bandwidth
+
+
+def host_info() -> dict:
+    """Core count and CPU model of the host running this process."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"host_cores": os.cpu_count(), "cpu_model": model}
 
 
 def peaks():
@@ -200,12 +228,11 @@ class ClockSampler:
 
 
 def cpu_baseline(args, seconds: float):
-    """The oracle's sequential decoder (one host thread) on a bounded sample
-    of the same workload: a 128 MiB copy sweep of the same recipe, decoded
-    repeatedly for about `seconds`."""
+    """The oracle's sequential decoder (one host thread) on the benchmark's
+    own workload (the same generated container), decoded repeatedly for
+    about `seconds`."""
     import oracle
-    sample = min(args.total, 128 << 20)
-    sw = make_workload(sample, args.block_size, args.L, seed_offset=1)
+    sw = make_workload(args.total, args.block_size, args.L)
     c = oracle.pack_sweep(sw, tags=False)
     oracle.decode(c)  # warm
     n, t0 = 0, time.perf_counter()
@@ -215,10 +242,10 @@ def cpu_baseline(args, seconds: float):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    gbs = n * sample / el / 1e9
-    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sample >> 20} MiB copy sweep (L={args.L}, same recipe), decoded {n} times "
-                      f"in {el:.1f} s by the sequential oracle decoder"}
+    gbs = n * args.total / el / 1e9
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", **host_info(),
+            "sample": f"the benchmark workload ({args.total >> 20} MiB copy sweep, L={args.L}), decoded {n} "
+                      f"times in {el:.1f} s by the sequential oracle decoder on one host thread"}
 
 
 def run_reference(args):
@@ -229,14 +256,15 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    sample = min(args.total, 128 << 20)
-    sw = make_workload(sample, args.block_size, args.L, seed_offset=1)
+    sample = args.total
+    sw = make_workload(sample, args.block_size, args.L)
     c = oracle.pack_sweep(sw, tags=False)
     t0 = time.perf_counter()
     for _ in range(max(1, args.warmup)):
         oracle.decode(c)
     per = (time.perf_counter() - t0) / max(1, args.warmup)
     if per * args.steps > 120.0:
+        # a bounded sample of the same recipe, so K steps take about 2 min
         sample = max(1 << 20, int(sample * 120.0 / (per * args.steps)) & ~((1 << 20) - 1))
         sw = make_workload(sample, args.block_size, args.L, seed_offset=1)
         c = oracle.pack_sweep(sw, tags=False)
@@ -246,9 +274,10 @@ def run_reference(args):
         oracle.decode(c)
     el = time.perf_counter() - t0
     gbs = args.steps * sample / el / 1e9
-    cb = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-          "sample": f"{sample >> 20} MiB copy sweep (L={args.L}, same recipe) per step, "
-                    f"{args.steps} steps in {el:.1f} s, sequential oracle decoder"}
+    cb = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", **host_info(),
+          "sample": f"{sample >> 20} MiB copy sweep (L={args.L}, same recipe"
+                    f"{'' if sample == args.total else ', a bounded sample of the workload'}) per step, "
+                    f"{args.steps} steps in {el:.1f} s, sequential oracle decoder on one host thread"}
     line = {
         "impl": "reference",
         "metric": f"match-phase decode output GB/s (copy sweep, L={args.L})",
@@ -256,7 +285,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u8", "data": "synthetic",
-        "config": workload_config(args, None),
+        "config": workload_config(args, {"same_config": sample == args.total}),
         "cpu_baseline": cb,
         "e2e": {"value": cb["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -275,7 +304,112 @@ def workload_config(args, extra):
 
 
 MODE = {"auto": 2, "waves": 0, "persistent": 1}
+LIB_RANGE_BYTES = 20480  # the work-range size an upload picks
 KERNEL = {0: "k_wave_copy (one launch per wave >= 1)", 1: "k_ranges (persistent, deferred matches)"}
+
+
+def sweep_leg(args, dev, st, peak):
+    """Table II's experiment over the match length: the same 1 GiB recipe at
+    each L of --sweep, decoded in the library's automatic mode (per-wave
+    kernels for short matches, the persistent staged schedule for long
+    ones), CUDA-event timed with the L2 flushed between steps."""
+    import torch
+    from paper_2607_18541_gb300 import aclz
+    Ls = [int(v) for v in args.sweep.split(",") if v.strip()]
+    rows = []
+    if not Ls:
+        return rows
+    out = torch.empty(((args.total + 15) // 16) * 16, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for L in Ls:
+        sw = make_workload(args.total, args.block_size, L)
+        c = aclz.aclz_pack(sw.total, sw.block_size, (4, 4, 4, 4), sw.blk_ntok, sw.lit_len, sw.match_len,
+                           sw.src, sw.literals)
+        h = aclz.aclz_upload(c, st)
+        try:
+            if args.range_bytes != LIB_RANGE_BYTES:
+                aclz.aclz_set_range_bytes(h, args.range_bytes, st)
+            info = aclz.aclz_handle_info(h)
+            cfg = dict(G=args.G, mode=MODE["auto"], ctas_per_sm=args.ctas_per_sm)
+            plan, launches = aclz.aclz_decode_plan(h, **cfg)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.sweep_steps)]
+            with torch.cuda.stream(st):
+                for _ in range(3):
+                    aclz.aclz_decode_all(h, out, stream=st, **cfg)
+                for i, (a, b) in enumerate(ev):
+                    if not args.no_flush:
+                        flush.fill_(i & 0xff)
+                    a.record(st)
+                    aclz.aclz_decode_all(h, out, stream=st, **cfg)
+                    b.record(st)
+                st.synchronize()
+            assert aclz.aclz_device_status(h, st) == 0
+            ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+            abytes = algorithmic_bytes(sw)
+            rows.append({"L": L, "value": round(sw.total / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+                         "ms_per_step": round(ms, 4), "step_frac": round(abytes / (ms * 1e-3) / 1e9 / peak, 4),
+                         "algorithmic_bytes_per_step": abytes, "mode": "persistent" if plan["mode"] == 1 else "waves",
+                         "n_waves": info.n_waves, "launches_per_step": launches,
+                         "paper_h100_context": PAPER_H100.get(L)})
+        finally:
+            aclz.aclz_free(h)
+    del out, flush
+    return rows
+
+
+def seek_leg(args, dev):
+    """The serving configuration: order-3 Markov word text (50k-word Zipf
+    vocabulary) of --seek-gib GiB, encoded at 12/16/24/32 in 64 KiB blocks,
+    held compressed in HBM; region seeks of log-uniform 16 KiB-256 MiB at
+    Poisson arrivals (25/50/75/90% of the saturated rate), admitted by free
+    HBM and served by the continuous-batching loop.  Every saturated-run
+    result is then compared on the device with the corpus slice it names."""
+    import torch
+    from paper_2607_18541_gb300 import aclz, serve, synth
+    total = int(args.seek_gib * (1 << 30))
+    t0 = time.perf_counter()
+    x, c = serve.build_corpus(total, chain_depth=4)
+    t_build = time.perf_counter() - t0
+    st = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    h = aclz.aclz_upload(c, st, flags=aclz.ACLZ_UPLOAD_FLATTEN)
+    t_up = time.perf_counter() - t0
+    try:
+        rows = serve.serve_benchmark(h, total, args.seek_requests)
+        # every result of the saturated request set against the corpus
+        xd = torch.from_numpy(x).to(dev)
+        del x
+        lo, hi = 16 << 10, min(256 << 20, total)
+        _, starts, sizes = synth.requests(args.seek_requests, 1.0, lo, hi, total, synth.SEED_SERVE + 7)
+        bad = []
+
+        def check(i, buf):
+            a, n = int(starts[i]), int(sizes[i])
+            if not torch.equal(buf[:n], xd[a:a + n]):
+                bad.append(i)
+
+        free, _ = torch.cuda.mem_get_info()
+        srv = serve.Server(h, int(free * 0.5))
+        srv.run(np.zeros(args.seek_requests), starts, sizes, on_done=check)
+        assert aclz.aclz_device_status(h, st) == 0
+        del xd
+    finally:
+        aclz.aclz_free(h)
+    sat = rows[0]
+    loads = [r for r in rows[1:]]
+    p50 = max(r["p50_ms"] for r in loads) if loads else sat["p50_ms"]
+    return {"workload": f"serve_wordtext_{args.seek_gib:g}GiB_64KiB_blocks",
+            "corpus_bytes": total, "container_bytes": int(c.size), "block_size": 1 << 16,
+            "thresholds": "12/16/24/32", "request_sizes": "log-uniform 16 KiB-256 MiB",
+            "requests_per_load": args.seek_requests, "saturated_gbs": sat["gbs"],
+            "p50_ms": {str(r["load"]): r["p50_ms"] for r in rows},
+            "p99_ms": {str(r["load"]): r["p99_ms"] for r in rows},
+            "gbs": {str(r["load"]): r["gbs"] for r in rows},
+            "clock_bias_ms_max": max(r["clock_bias_ms"] for r in rows),
+            "verified_requests": args.seek_requests - len(bad), "mismatched_requests": len(bad),
+            "corpus_build_s": round(t_build, 1), "upload_s": round(t_up, 2),
+            "latency": "GPU completion event minus Poisson arrival (host clock), per request"}
 
 
 def run_ours(args):
@@ -295,7 +429,8 @@ def run_ours(args):
     abytes = algorithmic_bytes(sw)
     st = torch.cuda.Stream(device=dev)
     h = aclz.aclz_upload(c, st)
-    aclz.aclz_set_range_bytes(h, args.range_bytes, st)
+    if args.range_bytes != LIB_RANGE_BYTES:
+        aclz.aclz_set_range_bytes(h, args.range_bytes, st)
     info = aclz.aclz_handle_info(h)
     cfg = dict(G=args.G, mode=MODE[args.mode], ctas_per_sm=args.ctas_per_sm)
     plan, launches_per_step = aclz.aclz_decode_plan(h, **cfg)
@@ -356,21 +491,33 @@ def run_ours(args):
     c_tagged = aclz.aclz_export(h)
     host_c = torch.from_numpy(c_tagged).pin_memory()
     host_out = torch.empty(sw.total, dtype=torch.uint8).pin_memory()
-    e2e_ms = []
-    with torch.cuda.stream(st):
-        for i in range(args.e2e_steps + 1):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            hh = aclz.aclz_upload(host_c.numpy(), st)
-            aclz.aclz_set_range_bytes(hh, args.range_bytes, st)
-            aclz.aclz_decode_all(hh, out, stream=st, **cfg)
-            host_out.copy_(out[:sw.total], non_blocking=True)
-            st.synchronize()
-            dt = time.perf_counter() - t0
-            aclz.aclz_free(hh)
-            if i:
-                e2e_ms.append(dt * 1e3)
-    e2e_val = replica_value(max_over_ranks(statistics.mean(e2e_ms), dev), sw.total, world)
+    def e2e_steps(container, steps):
+        ms, up = [], []
+        with torch.cuda.stream(st):
+            for i in range(steps + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                hh = aclz.aclz_upload(container, st)
+                if args.range_bytes != LIB_RANGE_BYTES:
+                    aclz.aclz_set_range_bytes(hh, args.range_bytes, st)
+                t1 = time.perf_counter()
+                aclz.aclz_decode_all(hh, out, stream=st, **cfg)
+                host_out.copy_(out[:sw.total], non_blocking=True)
+                st.synchronize()
+                dt = time.perf_counter() - t0
+                aclz.aclz_free(hh)
+                if i:
+                    ms.append(dt * 1e3)
+                    up.append((t1 - t0) * 1e3)
+        return statistics.mean(ms), statistics.mean(up)
+
+    e2e_mean, e2e_up = e2e_steps(host_c.numpy(), args.e2e_steps)
+    e2e_val = replica_value(max_over_ranks(e2e_mean, dev), sw.total, world)
+    # the same through an upload of the untagged container, whose minimal
+    # wave tags the upload computes (an ordered pass over the blocks)
+    host_u = torch.from_numpy(c).pin_memory()
+    ut_mean, ut_up = e2e_steps(host_u.numpy(), 1)
+    ut_val = replica_value(max_over_ranks(ut_mean, dev), sw.total, world)
     if rank == 0:
         line = {
             "metric": f"match-phase decode output GB/s (copy sweep, L={args.L})",
@@ -382,6 +529,8 @@ def run_ours(args):
                                              "algorithmic_bytes_per_step": abytes}),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kern,
+                         "achieved_is": "algorithmic bytes of the kernel per launch / its CUDA-event time",
+                         "rated_peak": RATED_HBM_GBS, "frac_of_rated": round(achieved / RATED_HBM_GBS, 4),
                          "launches_per_step": klaunch, "algorithmic_bytes_per_step": kbytes,
                          "ms_per_step": round(kms, 5), "peak_kind": f"{peak_kind} copy (burst)"},
             "phases": {"wave0_ms": round(w0_ms, 5), "wave0_bytes": w0_bytes,
@@ -392,14 +541,23 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "e2e": {"value": round(e2e_val, 2), "unit": "GB/s", "h2d_bytes_per_step": int(c_tagged.size),
                     "d2h_bytes_per_step": int(sw.total), "steps": args.e2e_steps,
+                    "ms_per_step": round(e2e_mean, 3), "upload_ms": round(e2e_up, 3),
                     "includes": "upload of the tagged container (copy, validation, tag check, worklists), "
-                                "decode, read-back of the output"},
+                                "decode, read-back of the output",
+                    "untagged_upload": {"value": round(ut_val, 2), "unit": "GB/s", "ms_per_step": round(ut_mean, 3),
+                                        "upload_ms": round(ut_up, 3), "h2d_bytes_per_step": int(c.size),
+                                        "includes": "upload of the container without wave tags (the upload "
+                                                    "computes minimal tags), decode, read-back"}},
             "paper_h100_context": {"value": PAPER_H100.get(args.L), "unit": "GB/s",
                                    "what": "purecopy.cu synthetic copy, 1 GB, H100 (Table II)"},
             "wall_s_timed": round(t_wall, 3),
         }
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds)
+            if args.sweep.strip():
+                line["sweep"] = sweep_leg(args, dev, st, peak)
+            if args.seek_gib > 0:
+                line["seek"] = seek_leg(args, dev)
         print(json.dumps(line), flush=True)
     aclz.aclz_free(h)
     if world > 1:

@@ -7,8 +7,12 @@ to the budget), admits queued requests in arrival order while their output
 buffers fit in the free-HBM budget and the in-flight slots, and launches the
 newly admitted ones together in one range-decode launch on the next of
 several CUDA streams, so batches that arrive while others run overlap on the
-device.  Completion times come from CUDA events, so latency = GPU completion
-- arrival, on one clock.
+device.  Latency = completion - arrival takes each term from its own clock:
+arrivals are host times from the start of the run, completions are CUDA
+event times from an event recorded, and waited for, just before the run
+starts.  The event therefore precedes the host start by at most the time
+that wait took (reported as clock_bias_ms), so a latency is overstated by at
+most that much and is never understated.
 
 In the paper a seek reads any region of a stream that stays compressed in
 GPU memory, decoding only that region (abstract; Sec. I); this loop serves
@@ -59,10 +63,11 @@ class Server:
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.next_stream = 0
 
-    def run(self, arrivals, starts, sizes, keep_outputs: bool = False):
+    def run(self, arrivals, starts, sizes, keep_outputs: bool = False, on_done=None):
         """Serve requests i = 0..n-1 arriving at arrivals[i] seconds (from
         the start of the run).  Returns per-request latency (s), makespan,
-        and optionally the outputs (host copies)."""
+        and optionally the outputs (host copies).  on_done(i, buf), when
+        given, sees each result's device buffer as its batch retires."""
         torch = self.torch
         n = len(arrivals)
         order = np.argsort(arrivals, kind="stable")
@@ -74,7 +79,10 @@ class Server:
         t_start_ev = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         t_start_ev.record(torch.cuda.current_stream())
+        tw = time.perf_counter()
+        t_start_ev.synchronize()  # the event precedes t0 by at most this wait
         t0 = time.perf_counter()
+        self.clock_bias_s = t0 - tw
         nxt = 0
         served = 0
         while served < n:
@@ -91,6 +99,8 @@ class Server:
                         done_t[i] = tdone
                         if keep_outputs:
                             outputs[i] = b[:int(sizes[i])].cpu().numpy()
+                        if on_done is not None:
+                            on_done(i, b)
                     used -= nbytes
                     served += len(idx)
                 else:
@@ -158,13 +168,15 @@ def serve_benchmark(h: int, corpus_len: int, n_requests: int, loads=(0.25, 0.5, 
     zero = np.zeros(n_requests)
     lat, span, _ = srv.run(zero, st, sz)
     sat_bps = float(sz.sum()) / span
-    rows.append(dict(load="saturated", requests=n_requests, gbs=round(sat_bps / 1e9, 2), **percentiles(lat)))
+    rows.append(dict(load="saturated", requests=n_requests, gbs=round(sat_bps / 1e9, 2),
+                     clock_bias_ms=round(srv.clock_bias_s * 1e3, 4), **percentiles(lat)))
     for f in loads:
         rate = f * sat_bps / mean_size
         arr, st, sz = synth.requests(n_requests, rate, lo, min(hi, corpus_len), corpus_len, seed + int(f * 100))
         lat, span, _ = srv.run(arr, st, sz)
         rows.append(dict(load=f, offered_req_per_s=round(rate, 2), requests=n_requests,
-                         gbs=round(float(sz.sum()) / span / 1e9, 2), **percentiles(lat)))
+                         gbs=round(float(sz.sum()) / span / 1e9, 2), clock_bias_ms=round(srv.clock_bias_s * 1e3, 4),
+                         **percentiles(lat)))
     return rows
 
 

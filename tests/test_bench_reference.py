@@ -25,4 +25,6 @@ def test_reference_arm_prints_one_contract_line():
     assert d["config"]["workload"] == "copy_sweep_1024MiB_L1024"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["host_cores"] >= 1 and "cpu_model" in cb
+    assert d["config"]["same_config"] is True  # two steps of the full workload fit the time bound
     assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
