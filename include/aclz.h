@@ -168,6 +168,15 @@ int aclz_upload_ex(const void *host_buf, uint64_t n, uint32_t flags, void *strea
  * words and end every state at 2^16; then as aclz_upload_ex. */
 int aclz_upload_acle(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out);
 
+/* aclz_upload_acle that also records two caller events (cudaEvent_t, each
+ * created by the caller, or NULL) on the stream: ev_begin just before the
+ * device tile decode (after the copies to the device) and ev_end after the
+ * byte planes are turned into tokens, so the entropy stage can be timed
+ * alone.  A measurement aid; the paper times its entropy stage apart from
+ * the match phase as well (ANS 9% / match 91%, Sec. V). */
+int aclz_upload_acle_ev(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out,
+                        void *ev_begin, void *ev_end);
+
 /* Host side of the entropy stage: the ACLE form (layout above) of the v1
  * container host_container[0, n).  Each 64 KiB tile of each stream is coded
  * on its own (frequencies: the only byte value present takes all of 2^12;

@@ -117,6 +117,7 @@ _SIGS = [
 ]
 OPTIONAL_SIGS: list = [  # entry points added by later modules register here
     ("aclz_fnv_noalloc", _I, [_VP, _U64, _U64P, _VP]),
+    ("aclz_upload_acle_ev", _I, [_VP, _U64, _U32, _VP, ctypes.POINTER(_VP), _VP, _VP]),
 ]
 
 

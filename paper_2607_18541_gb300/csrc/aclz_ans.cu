@@ -139,6 +139,7 @@ struct AcleCtx {
     uint64_t pay_bytes = 0;
     std::vector<TileDesc> tiles;
     uint64_t plane_bytes = 0;
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // optional: around the tile decode
 };
 
 int fill_from_acle(aclz_handle *h, const View &v, const void *ctx, void *stream) {
@@ -162,6 +163,7 @@ int fill_from_acle(aclz_handle *h, const View &v, const void *ctx, void *stream)
         ck(cudaMemsetAsync(d_err, 0, 4, st)) &&
         (!a.pay_bytes || ck(cudaMemcpyAsync(d_pay, a.pay, a.pay_bytes, cudaMemcpyHostToDevice, st))) &&
         (!nt || ck(cudaMemcpyAsync(d_td, a.tiles.data(), sizeof(TileDesc) * nt, cudaMemcpyHostToDevice, st)))) {
+        if (a.ev_begin) ck(cudaEventRecord(a.ev_begin, st));
         if (nt) {
             const unsigned grid = (unsigned)((nt + kWarps - 1) / kWarps);
             k_ans_tiles<<<grid, kWarps * 32, kWarps * kWarpSmem, st>>>(d_pay, d_td, nt, d_planes, a.plane_bytes,
@@ -173,6 +175,7 @@ int fill_from_acle(aclz_handle *h, const View &v, const void *ctx, void *stream)
             k_planes_to_tokens<<<grid, 256, 0, st>>>(d_planes, v.n_tokens, (uint4 *)h->d_tok);
             ck(cudaGetLastError());
         }
+        if (a.ev_end) ck(cudaEventRecord(a.ev_end, st));
         uint32_t err = 0;
         if (rc == ACLZ_OK && ck(cudaMemcpyAsync(&err, d_err, 4, cudaMemcpyDeviceToHost, st)) &&
             ck(cudaStreamSynchronize(st)) && err)
@@ -186,7 +189,8 @@ int fill_from_acle(aclz_handle *h, const View &v, const void *ctx, void *stream)
 
 }  // namespace
 
-extern "C" int aclz_upload_acle(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out) {
+extern "C" int aclz_upload_acle_ev(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out,
+                                   void *ev_begin, void *ev_end) {
     if (!host_buf || !out) return ACLZ_E_INVAL;
     *out = nullptr;
     if (flags & ~(uint32_t)ACLZ_UPLOAD_FLATTEN) return ACLZ_E_INVAL;
@@ -242,5 +246,11 @@ extern "C" int aclz_upload_acle(const void *host_buf, uint64_t n, uint32_t flags
         }
     }
     if (a.tiles.size() != n_tiles) return ACLZ_E_CORRUPT;
+    a.ev_begin = (cudaEvent_t)ev_begin;
+    a.ev_end = (cudaEvent_t)ev_end;
     return upload_view(v, flags, stream, fill_from_acle, &a, out);
+}
+
+extern "C" int aclz_upload_acle(const void *host_buf, uint64_t n, uint32_t flags, void *stream, aclz_handle **out) {
+    return aclz_upload_acle_ev(host_buf, n, flags, stream, out, nullptr, nullptr);
 }

@@ -455,7 +455,11 @@ int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st, cudaEvent_t phas
         else
             k_wave_copy<G, ITEMS, false><<<grid, kThreads, 0, st>>>(t, n, out, h->log2_bs);
     }
-    return cudaGetLastError() == cudaSuccess ? ACLZ_OK : ACLZ_E_CUDA;
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
+        note_cuda_error(e);
+        return ACLZ_E_CUDA;
+    }
+    return ACLZ_OK;
 }
 
 struct Occ {
