@@ -98,6 +98,22 @@ int aclz_encode(const void *host_src, uint64_t n, const aclz_encode_params *p,
                 const uint8_t *block_min_match, int threads, void *host_out, uint64_t cap,
                 uint64_t *out_size);
 
+/* aclz_encode with the parse on the GPU (the paper's encoder is a CPU
+ * program and makes no speed claim, Sec. VI): the same container, byte for
+ * byte, from the same arguments.  Every candidate chain of the greedy parse
+ * is an ordered run of positions with one 4-byte prefix, so the device sorts
+ * the positions by (prefix, position), then parses every LZ block with one
+ * warp whose lanes score up to 32 candidates at a time, and lays the
+ * container out by scans.  host_src: n input bytes (host); n < 2^32 - 64
+ * (else ACLZ_E_UNSUPPORTED).  With host_out NULL only *out_size is set (the
+ * parse still runs); otherwise cap must hold *out_size bytes
+ * (ACLZ_E_CAPACITY).  Allocates device memory of about 25 bytes per input
+ * byte for the call (sorted prefixes, ranks, per-block token slots) and
+ * frees it before returning; synchronizes the stream. */
+int aclz_encode_gpu(const void *host_src, uint64_t n, const aclz_encode_params *p,
+                    const uint8_t *block_min_match, void *stream, void *host_out, uint64_t cap,
+                    uint64_t *out_size);
+
 /* Container from token arrays (host): blk_ntok[n_blocks] tokens per
  * block, lit_len/match_len/src per token, the literal bytes.  min_match is
  * recorded, not enforced.  No wave tags. */

@@ -118,6 +118,7 @@ _SIGS = [
 OPTIONAL_SIGS: list = [  # entry points added by later modules register here
     ("aclz_fnv_noalloc", _I, [_VP, _U64, _U64P, _VP]),
     ("aclz_upload_acle_ev", _I, [_VP, _U64, _U32, _VP, ctypes.POINTER(_VP), _VP, _VP]),
+    ("aclz_encode_gpu", _I, [_VP, _U64, ctypes.POINTER(aclz_encode_params), _VP, _VP, _VP, _U64, _U64P]),
 ]
 
 
@@ -199,6 +200,22 @@ def aclz_encode(src, params: aclz_encode_params, block_min_match=None, threads: 
     _ck(lib().aclz_encode(_hptr(x) if x.size else None, x.size, ctypes.byref(params),
                           None if bmm is None else bmm.ctypes.data_as(_U8P), threads, _hptr(out), cap,
                           ctypes.byref(size)), "aclz_encode")
+    return out[:size.value]
+
+
+def aclz_encode_gpu(src, params: aclz_encode_params, block_min_match=None, stream=None) -> np.ndarray:
+    """aclz_encode with the greedy parse on the GPU: the same container."""
+    x = _np_u8(src)
+    bmm = None
+    if block_min_match is not None:
+        bmm = np.ascontiguousarray(block_min_match, dtype=np.uint8)
+    size = ctypes.c_uint64(0)
+    bp = _hptr(bmm) if bmm is not None else None
+    _ck(lib().aclz_encode_gpu(_hptr(x), x.size, ctypes.byref(params), bp, _stream(stream), None, 0,
+                              ctypes.byref(size)), "aclz_encode_gpu")
+    out = np.empty(max(1, size.value), dtype=np.uint8)
+    _ck(lib().aclz_encode_gpu(_hptr(x), x.size, ctypes.byref(params), bp, _stream(stream), _hptr(out), out.size,
+                              ctypes.byref(size)), "aclz_encode_gpu")
     return out[:size.value]
 
 
