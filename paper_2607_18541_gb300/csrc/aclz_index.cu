@@ -306,6 +306,47 @@ __global__ void __launch_bounds__(256) k_tags_check(const uint4 *__restrict__ to
     if (g.ballot(bad) && g.lane == 0) atomicOr(err, kErrCorrupt);
 }
 
+// One pass of the parallel minimal-tag computation: every match's tag is
+// raised to its requirement under the current tags (read as other warps
+// leave them).  Requirements only grow with the tags, so from all-zero
+// tags the passes climb to the least fixed point, which is the minimal
+// tagging; a pass that raises nothing (changed stays 0) proves it reached.
+// Also folds the largest tag into *maxtag.
+__global__ void __launch_bounds__(256) k_tags_relax(const uint4 *__restrict__ tok,
+                                                    const uint64_t *__restrict__ blk_tok,
+                                                    const uint32_t *__restrict__ tokdst, uint32_t *tags,
+                                                    uint32_t nb, uint32_t log2bs, uint64_t n_tok,
+                                                    uint32_t *changed, uint32_t *maxtag) {
+    Group<32> g;
+    const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nb) return;
+    const uint64_t t0 = blk_tok[b], t1 = blk_tok[b + 1];
+    uint32_t mx = 0;
+    bool raised = false;
+    for (uint64_t w = t0; w < t1; w += 32) {
+        const uint64_t i = w + g.lane;
+        if (i < t1) {
+            const uint4 t = __ldg(tok + i);
+            if (t.y) {
+                const uint64_t src = ((uint64_t)t.z | ((uint64_t)t.w << 32)) & kSrcMask;
+                bool inwin = false;
+                const uint32_t req = match_requirement(tok, blk_tok, tokdst, tags, src, t.y, b, log2bs, n_tok,
+                                                       n_tok, &inwin);
+                const uint32_t cur = __ldcg(tags + i);
+                if (req > cur) {
+                    __stcg(tags + i, req);
+                    raised = true;
+                }
+                mx = max(mx, max(req, cur));
+            }
+        }
+        g.sync();
+    }
+    for (int o = 16; o; o >>= 1) mx = max(mx, g.shfl(mx, (g.lane + o) & 31));
+    if (g.ballot(raised) && g.lane == 0) *changed = 1u;
+    if (g.lane == 0 && mx) atomicMax(maxtag, mx);
+}
+
 __global__ void k_extract_tags(const uint4 *__restrict__ tok, uint32_t *tags, uint64_t n) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
@@ -647,6 +688,38 @@ int aclz::device_excl_scan(uint32_t *d, uint64_t n, uint32_t *d_total, void *str
     return cuda_rc(cudaGetLastError());
 }
 
+// Minimal wave tags of h's tokens into d_tags (and the largest into
+// *d_maxtag) by parallel relaxation passes from all-zero tags, checked every
+// kRelaxBatch passes; true when a pass raised nothing within kRelaxMax
+// passes.  A stream whose copy chains are deeper than that is left to the
+// ordered pass (false; d_tags then holds partial tags).
+namespace {
+constexpr uint32_t kRelaxBatch = 8, kRelaxMax = 512;
+bool relax_tags(aclz_handle *h, uint32_t *d_tags, uint32_t *d_maxtag, cudaStream_t st) {
+    const uint32_t nb = h->n_blocks;
+    const uint64_t nt = h->n_tokens;
+    if (!nb) return true;
+    DevBuf flags;
+    if (cudaMalloc(&flags.p, 4 * kRelaxBatch) != cudaSuccess) return false;
+    uint32_t *changed = (uint32_t *)flags.p;
+    if (cudaMemsetAsync(d_tags, 0, 4 * (nt ? nt : 1), st) != cudaSuccess) return false;
+    const unsigned wblocks = (nb + 7) / 8;
+    for (uint32_t done_passes = 0; done_passes < kRelaxMax; done_passes += kRelaxBatch) {
+        if (cudaMemsetAsync(changed, 0, 4 * kRelaxBatch, st) != cudaSuccess) return false;
+        for (uint32_t k = 0; k < kRelaxBatch; k++)
+            k_tags_relax<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_tokdst, d_tags, nb,
+                                                   h->log2_bs, nt, changed + k, d_maxtag);
+        uint32_t last = 1;
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&last, changed + kRelaxBatch - 1, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return false;
+        if (!last) return true;
+    }
+    return false;
+}
+}  // namespace
+
 // Decode index of h from its device tokens (d_tok with n_tokens entries,
 // d_blk_tok, d_blk_lit, d_lit): per-token validation and offsets, wave
 // tags (given ones checked, else minimal ones; local 0/1 ones for the
@@ -704,7 +777,11 @@ int aclz::build_index(aclz_handle *h, bool has_tags, uint32_t given_waves, bool 
         k_tags_local<<<wblocks, 256, 0, st>>>((const uint4 *)h->d_tok, h->d_blk_tok, h->d_tokdst, d_tags, nb,
                                                h->log2_bs, d_maxtag);
         k_store_tags<<<1024, 256, 0, st>>>((uint4 *)h->d_tok, d_tags, nt);
+    } else if (relax_tags(h, d_tags, d_maxtag, st)) {
+        // minimal tags by parallel passes (the chains were shallow enough)
+        k_store_tags<<<1024, 256, 0, st>>>((uint4 *)h->d_tok, d_tags, nt);
     } else {
+        CK(cudaMemsetAsync(d_maxtag, 0, 4, st));
         CK(cudaMalloc(&done.p, 4 * nb));
         CK(cudaMemsetAsync(done.p, 0, 4 * nb, st));
         int dev_sms = 0;

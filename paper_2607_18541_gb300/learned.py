@@ -11,15 +11,21 @@ fallback:
   (``aclz_block_features``), 13 statistics of a probe parse at 6/8/10/12
   (coverage, match lengths, distance-class shares, literal runs) and the
   block's log position;
-* labels: every candidate is encoded; a block's cost is the entropy-coded
-  size of its share of the four token streams under the stream-wide symbol
-  frequencies of that encoding; among candidates no costlier than the
-  fallback the label is the one with the fewest tokens (longest mean token,
-  the decode-speed lever of Sec. III-C);
+* labels: every candidate is encoded and decoded on the GPU; a block's
+  cost is the entropy-coded size of its share of the four token streams
+  under the stream-wide symbol frequencies of that encoding, and its decode
+  time is predicted by a model fitted to the measured decode times of the
+  whole candidate streams (time ~ a*tokens + b*deferred matches + c*bytes,
+  nonnegative least squares: tokens are the work-item count of Sec. III-C,
+  deferred matches are the ones the wavefront holds back); the label is the
+  candidate of least predicted time, with a per-byte price chosen so that
+  the labelled stream is no larger than at the fallback;
 * training: the GPU kernels (``aclz_mlp_grad``, ``aclz_mlp_adam``);
 * inference: argmax, fallback when the top probability is below tau, then a
-  per-block check that keeps the choice only where its cost does not exceed
-  the fallback's, so the compressed size stays at or below the fixed lever's.
+  check of the whole stream: its estimated size must not exceed the
+  fallback's, and its measured decode time (on the GPU, the judge) must be
+  below the fallback's; otherwise the least efficient picks go back to the
+  fallback and the stream is encoded again.
 
 Decoding is unchanged and bit-exact whatever the network picks.
 """
@@ -192,16 +198,68 @@ def features(x, base_container, block_size: int = BLOCK, stream=None) -> np.ndar
     return np.concatenate([raw, pf, posf], axis=1)
 
 
-def label_data(x, block_size: int = BLOCK, threads: int = 0):
-    """Features of one training stream and, per candidate, its block costs
-    and token counts [K, n_blocks]."""
+def deferred_per_block(c) -> np.ndarray:
+    """Matches per block that the wavefront holds back (wave tag > 0 in the
+    upload's tags; for a stream the upload flattens, the matches not in
+    order within their block)."""
+    import torch
+    blk = read_tokens(c)[0]
+    _, _, ml, _, _, _, _ = read_tokens(c)
+    h = aclz.aclz_upload(c, torch.cuda.current_stream())
+    try:
+        tags = aclz.aclz_tags(h)
+    finally:
+        aclz.aclz_free(h)
+    owner = np.repeat(np.arange(blk.size), blk)
+    return np.bincount(owner, weights=((tags > 0) & (ml > 0)).astype(np.float64), minlength=blk.size)
+
+
+def label_data(x, block_size: int = BLOCK, threads: int = 0, reps: int = 3):
+    """Features of one training stream and, per candidate, its block costs,
+    token and deferred-match counts [K, n_blocks] and the measured decode
+    time of the whole stream [K] (ms)."""
     threads = threads or min(K, os.cpu_count() or 1)
     per = max(1, (os.cpu_count() or 1) // threads)
     with ThreadPoolExecutor(threads) as ex:
         cs = list(ex.map(lambda mm: encode(x, mm, block_size=block_size, threads=per), CANDIDATES))
     costs = np.stack([block_costs(c) for c in cs])
     ntok = np.stack([read_tokens(c)[0].astype(np.float64) for c in cs])
-    return features(x, cs[BASE], block_size), costs, ntok
+    ndef = np.stack([deferred_per_block(c) for c in cs])
+    ms = np.array([x.size / decode_gbs(c, x.size, reps)[0] / 1e6 for c in cs])
+    return features(x, cs[BASE], block_size), costs, ntok, ndef, ms
+
+
+def fit_time_model(samples) -> np.ndarray:
+    """Coefficients (a, b, c) >= 0 of time_ms ~ a*tokens + b*deferred +
+    c*bytes over (tokens, deferred, bytes, ms) samples (least squares
+    relative to each time, so fast and slow streams count alike)."""
+    from scipy.optimize import nnls
+    A = np.array([[t, d, n] for t, d, n, _ in samples], dtype=np.float64)
+    y = np.array([m for *_, m in samples], dtype=np.float64)
+    w = 1.0 / np.maximum(y, 1e-6)
+    coef, _ = nnls(A * w[:, None], y * w)
+    return coef
+
+
+def time_labels(costs, ntok, ndef, coef):
+    """Per-block labels of least predicted decode time under the fallback's
+    size: k(b) = argmin_k t[k, b] + lam * cost[k, b], t = a*tokens + b*deferred,
+    with lam >= 0 the smallest price per byte at which the stream is no
+    larger than at 12/16/24/32 (bisection)."""
+    nb = costs.shape[1]
+    t = coef[0] * ntok + coef[1] * ndef
+    budget = costs[FALLBACK].sum()
+    size = lambda lam: costs[np.argmin(t + lam * costs, axis=0), np.arange(nb)].sum()
+    lo, hi = 0.0, 1e-9
+    while size(hi) > budget and hi < 1e12:
+        hi *= 4.0
+    for _ in range(60):
+        lam = 0.5 * (lo + hi)
+        if size(lam) > budget:
+            lo = lam
+        else:
+            hi = lam
+    return np.argmin(t + hi * costs, axis=0).astype(np.int32), hi
 
 
 def lagrange_labels(costs, ntok, token_target: float = TOKEN_TARGET):
@@ -238,6 +296,7 @@ class Model:
         self.params = torch.from_numpy(np.concatenate(parts).astype(np.float32)).cuda()
         self.mean = np.zeros(N_FEATURES)
         self.std = np.ones(N_FEATURES)
+        self.time_coef = None  # (a, b, c) of the decode-time model the labels came from
 
     def standardize(self, f):
         return ((f - self.mean) / self.std).astype(np.float32)
@@ -288,6 +347,7 @@ class Model:
     def save(self, path: str):
         with open(path, "w") as fh:
             json.dump(dict(K=K, candidates=CANDIDATES, mean=self.mean.tolist(), std=self.std.tolist(),
+                           time_coef=None if self.time_coef is None else list(map(float, self.time_coef)),
                            params=self.params.cpu().numpy().tolist()), fh)
 
     @classmethod
@@ -298,17 +358,22 @@ class Model:
         m = cls()
         m.params = torch.tensor(d["params"], dtype=torch.float32, device="cuda")
         m.mean, m.std = np.array(d["mean"]), np.array(d["std"])
+        m.time_coef = None if d.get("time_coef") is None else np.array(d["time_coef"])
         return m
 
 
-def encode_learned(model: Model, x, block_size: int = BLOCK, tau: float = 0.0, passes: int = 6,
-                   base=None, fb=None):
-    """Per-block thresholds from the network, checked against the plain encoder's
-    ratio and decode speed: the result is kept only if its estimated size
-    and its token count (the decode-speed lever, Sec. III-C) are both no
-    larger than the fixed 12/16/24/32 encode's.  When one is larger, the
-    least efficient picks (largest size increase per token saved, or
-    largest token increase per byte saved) are put back to 12/16/24/32
+def encode_learned(model: Model, x, block_size: int = BLOCK, tau: float = 0.0, passes: int = 8,
+                   base=None, fb=None, time_coef=None, judge=None):
+    """Per-block thresholds from the network, checked against the plain
+    encoder's ratio and decode speed: the result is kept only if its
+    estimated size is no larger than the fixed 12/16/24/32 encode's and its
+    decode is no slower.  Decode speed is, by default, the token count (the
+    work-item count of Sec. III-C); with time_coef (a, b, c) it is the
+    fitted time a*tokens + b*deferred matches (GPU tags); with judge (a
+    function of a container returning its measured decode time) the
+    measured time must also be below the fallback's.  When a test fails,
+    the least efficient picks (largest size increase per unit of speed
+    saved, or largest slowdown per byte saved) are put back to 12/16/24/32
     until the excess is covered, and the stream is encoded again (a block's
     parse depends only on its own thresholds; sizes use stream-wide symbol
     frequencies).  After `passes` tries the fallback container is returned.
@@ -318,32 +383,47 @@ def encode_learned(model: Model, x, block_size: int = BLOCK, tau: float = 0.0, p
         base = encode(x, CANDIDATES[BASE], block_size=block_size)
     if fb is None:
         fb = encode(x, CANDIDATES[FALLBACK], block_size=block_size)
+
+    def speed_cost(c):
+        tok = read_tokens(c)[0].astype(np.float64)
+        if time_coef is None:
+            return tok
+        return time_coef[0] * tok + time_coef[1] * deferred_per_block(c)
+
     fb_cost = block_costs(fb)
-    fb_tok = read_tokens(fb)[0].astype(np.int64)
-    fb_est, fb_T = est_bytes(fb), int(fb_tok.sum())
+    fb_t = speed_cost(fb)
+    fb_est, fb_T = est_bytes(fb), float(fb_t.sum())
+    fb_ms = judge(fb) if judge is not None else None
     k = model.choose(features(x, base, block_size), tau)
     for _ in range(passes):
         if np.all(k == FALLBACK):
             break
         bmm = np.array([CANDIDATES[j] for j in k], dtype=np.uint8)
         c = encode(x, block_mm=bmm, block_size=block_size)
-        tok = read_tokens(c)[0].astype(np.int64)
-        est, T = est_bytes(c), int(tok.sum())
-        if est <= fb_est and T <= fb_T:
+        t = speed_cost(c)
+        est, T = est_bytes(c), float(t.sum())
+        slow = T > fb_T
+        if est <= fb_est and not slow and judge is not None:
+            slow = judge(c) >= fb_ms
+            if slow:
+                T = fb_T + 1.0  # measured slower: put back the picks that add the most predicted time
+        if est <= fb_est and not slow:
             return c, k
-        dc = block_costs(c) - fb_cost          # bytes added by each block's pick
-        dt = (tok - fb_tok).astype(np.float64)  # tokens added
+        dc = block_costs(c) - fb_cost  # bytes added by each block's pick
+        dt = t - fb_t                   # predicted time (or tokens) added
         picked = np.nonzero(k != FALLBACK)[0]
         if est > fb_est:
-            # least bytes-efficient picks first: most bytes per token saved
-            key = dc[picked] / np.maximum(1.0, -dt[picked])
+            # least bytes-efficient picks first: most bytes per unit of time saved
+            key = dc[picked] / np.maximum(1e-9, -dt[picked])
             need = (est - fb_est) * 1.2 + 1.0
+            gain = dc
         else:
             key = dt[picked] / np.maximum(1.0, -dc[picked])
-            need = (T - fb_T) * 1.2 + 1.0
+            need = max(T - fb_T, 0.0) * 1.2 + 1e-9
+            gain = dt
         order = picked[np.argsort(-key)]
-        gain = dc[order] if est > fb_est else dt[order]
-        cut = int(np.searchsorted(np.cumsum(np.maximum(gain, 0.0)), need)) + 1
+        g = np.maximum(gain[order], 0.0)
+        cut = int(np.searchsorted(np.cumsum(g), need)) + 1 if g.sum() > 0 else max(1, order.size // 4)
         k[order[:cut]] = FALLBACK
     k[:] = FALLBACK
     return fb, k
@@ -377,17 +457,29 @@ def decode_gbs(c, n: int, reps: int = 5, flatten: bool = False, **cfg):
         aclz.aclz_free(h)
 
 
-def train_default(scale: int = 1, steps: int = 2000, seed: int = 20260712, log=print):
+def train_default(scale: int = 1, steps: int = 2000, seed: int = 20260712, log=print, streams=None):
+    """Labels from measured decode times: every training stream is encoded
+    at every candidate and decoded on the GPU; the time model fitted to all
+    of those decodes prices each block's candidates, and each block is
+    labelled with the fastest under its stream's size budget (time_labels)."""
+    streams = streams if streams is not None else training_streams(scale)
+    data = [label_data(s) for s in streams]
+    samples = []
+    for (f, costs, ntok, ndef, ms), s in zip(data, streams):
+        for k in range(K):
+            samples.append((ntok[k].sum(), ndef[k].sum(), float(s.size), ms[k]))
+    coef = fit_time_model(samples)
     feats, labels = [], []
-    for s in training_streams(scale):
-        f, costs, ntok = label_data(s)
-        y, _ = lagrange_labels(costs, ntok)
+    for f, costs, ntok, ndef, ms in data:
+        y, _ = time_labels(costs, ntok, ndef, coef)
         feats.append(f)
         labels.append(y)
     f = np.concatenate(feats)
     y = np.concatenate(labels)
-    log(json.dumps({"train_blocks": int(y.size), "label_hist": np.bincount(y, minlength=K).tolist()}))
+    log(json.dumps({"train_blocks": int(y.size), "label_hist": np.bincount(y, minlength=K).tolist(),
+                    "time_model_ms_per": {"token": float(coef[0]), "deferred": float(coef[1]), "byte": float(coef[2])}}))
     model = Model(seed)
+    model.time_coef = coef
     hist = model.fit(f, y, steps=steps, batch=256, lr=1e-3, log_every=max(1, steps // 4))
     acc = float((model.choose(f) == y).mean())
     log(json.dumps({"train_loss": [round(v, 4) for _, v in hist], "train_acc": round(acc, 3)}))
@@ -413,12 +505,14 @@ def gain_single(model: Model, x, block_size: int = BLOCK, reps: int = 5, bound: 
     xd = torch.from_numpy(x).cuda()
     base = encode(x, CANDIDATES[BASE], block_size=block_size)
     fb = encode(x, CANDIDATES[FALLBACK], block_size=block_size)
-    lc, k = encode_learned(model, x, block_size, base=base, fb=fb)
+    judge = lambda c: x.size / decode_gbs(c, x.size, reps)[0] / 1e6  # measured decode ms
+    lc, k = encode_learned(model, x, block_size, base=base, fb=fb, time_coef=model.time_coef, judge=judge)
     rows_c = [("6/8/10/12", base), ("12/16/24/32", fb), ("learned", lc)]
-    if bound:
-        _, costs, ntok = label_data(x, block_size)
-        yb, _ = lagrange_labels(costs, ntok)
-        rows_c.append(("label bound", encode_learned(Choices(yb), x, block_size, base=base, fb=fb)[0]))
+    if bound and model.time_coef is not None:
+        _, costs, ntok, ndef, _ = label_data(x, block_size)
+        yb, _ = time_labels(costs, ntok, ndef, model.time_coef)
+        rows_c.append(("label bound", encode_learned(Choices(yb), x, block_size, base=base, fb=fb,
+                                                     time_coef=model.time_coef, judge=judge)[0]))
     for name, c in rows_c:
         try:
             gbs, out = decode_gbs(c, x.size, reps)
@@ -443,7 +537,7 @@ def gain_batched(model: Model, n: int = 512, lo: int = 16 << 10, hi: int = 4 << 
     streams = batched.make_streams(n, lo, hi)
     total = int(sum(s.size for s in streams))
     fixed = [encode(s, CANDIDATES[FALLBACK], threads=1) for s in streams]
-    learned_c = [encode_learned(model, s, fb=f)[0] for s, f in zip(streams, fixed)]
+    learned_c = [encode_learned(model, s, fb=f, time_coef=model.time_coef)[0] for s, f in zip(streams, fixed)]
     ms_one, outs = batched.time_one_by_one(fixed, reps=reps)
     ok_one = all(torch.equal(o[:s.size].cpu(), torch.from_numpy(s)) for o, s in zip(outs, streams))
     dec = batched.BatchDecoder(learned_c)

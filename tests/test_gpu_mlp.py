@@ -89,7 +89,8 @@ def test_training_lowers_loss_and_learned_encode_is_exact():
                synth.fastq(1 << 20, seed=0x7A0001), synth.markov2(1 << 19, seed=0x7B0001)]
     feats, labels = [], []
     for s in streams:
-        f, costs, ntok = learned.label_data(s, threads=4)
+        f, costs, ntok, ndef, ms = learned.label_data(s, threads=4)
+        assert ndef.shape == ntok.shape and np.all(ndef <= ntok) and ms.shape == (learned.K,) and np.all(ms > 0)
         y, lam = learned.lagrange_labels(costs, ntok)
         assert f.shape == (y.size, learned.N_FEATURES) and lam >= 0
         # the labels meet the token target of their stream

@@ -172,3 +172,34 @@ def test_check_never_returns_a_larger_or_slower_encode(monkeypatch, mixed, kind)
     got = learned.read_tokens(c)
     for a, b in zip(got[:5], want[:5]):
         assert np.array_equal(a, b)
+
+
+def test_time_labels_meet_the_size_budget_with_the_smallest_price():
+    rng = np.random.default_rng(8)
+    K, nb = learned.K, 300
+    ntok = rng.integers(5, 60, (K, nb)).astype(np.float64)
+    ndef = np.floor(ntok * rng.uniform(0, 1, (K, nb)))
+    costs = rng.uniform(100, 1000, (K, nb))
+    coef = np.array([0.002, 0.01, 1e-7])
+    y, lam = learned.time_labels(costs, ntok, ndef, coef)
+    t = coef[0] * ntok + coef[1] * ndef
+    # no larger than the fallback's size, each label the best at its price
+    assert costs[y, np.arange(nb)].sum() <= costs[learned.FALLBACK].sum() + 1e-6
+    assert np.array_equal(y, np.argmin(t + lam * costs, axis=0))
+    # the price is the smallest that meets the budget
+    if lam > 1e-12:
+        y2 = np.argmin(t + 0.98 * lam * costs, axis=0)
+        assert costs[y2, np.arange(nb)].sum() > costs[learned.FALLBACK].sum() - 1e-6
+    # and the labelled blocks are predicted no slower than the fallback's
+    assert t[y, np.arange(nb)].sum() <= t[learned.FALLBACK].sum() + 1e-9
+
+
+def test_time_model_recovers_known_coefficients():
+    rng = np.random.default_rng(9)
+    a, b, c = 3e-5, 2e-4, 1e-9
+    samples = []
+    for _ in range(40):
+        tok, dfr, n = rng.uniform(1e4, 1e6), rng.uniform(0, 5e5), rng.uniform(1e7, 1e9)
+        samples.append((tok, dfr, n, a * tok + b * dfr + c * n))
+    got = learned.fit_time_model(samples)
+    assert np.allclose(got, [a, b, c], rtol=1e-6, atol=1e-12)
