@@ -34,8 +34,12 @@ using namespace aclz;
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnrollWave = 2;   // chunks per lane per round in the wave-0 pass
-constexpr int kUnrollCopy = 4;   // chunks per lane per round in match copies
+// chunks per lane per round in the wave-0 pass: before per-wave copies
+// (short matches; more resident warps without spills) and before the
+// persistent schedule (long in-order matches)
+constexpr int kUnrollWaveShort = 1, kUnrollWaveLong = 2;
+constexpr int kUnrollCopy = 2;   // chunks per lane per round in per-wave match copies
+constexpr int kUnrollRanges = 4; // the same in the persistent schedule's register copies
 // staged (TMA) copies: jobs of at least kTmaMin bytes, pieces of <= kPiece
 constexpr uint32_t kTmaMin = 192;
 constexpr uint32_t kPiece = 2048;
@@ -46,6 +50,8 @@ constexpr uint64_t kSmallWave = 155648;
 // per-wave copies put full chunks first when deferred matches average
 // at least this many bytes
 constexpr double kFullFirstMin = 48.0;
+// per-wave kernels are launched with programmatic stream serialization
+constexpr int kWavePdl = 1;
 
 __device__ __forceinline__ uint64_t tri_dst(const uint4 t) { return (uint64_t)t.x | ((uint64_t)(t.y & 0xffu) << 32); }
 __device__ __forceinline__ uint64_t tri_src(const uint4 t) { return (uint64_t)t.z | ((uint64_t)(t.w & 0xffu) << 32); }
@@ -56,6 +62,15 @@ __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long l
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+
+// Programmatic dependent launch (per-wave kernels): a kernel lets the next
+// kernel of its stream start once all of its CTAs have begun, and that
+// kernel reads nothing the previous one writes before griddep_wait, which
+// returns when the previous grid has completed and its writes are visible.
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Bounded waits: spin_limit polls (sleeping up to 256 ns each) before a wait
 // gives up.  The host scales it with the wave count, from 2^22 (about a
@@ -89,7 +104,7 @@ __device__ __forceinline__ bool wait_waves_below(const unsigned long long *done,
 // Wave 0 of one block: scan, literal runs, in-order (tag 0) matches, and
 // the deferred matches' triplets.  The next window's tokens are loaded
 // while the current window is copied.
-template <int G>
+template <int G, int UW>
 __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const uint4 *__restrict__ tok,
                                             const uint8_t *__restrict__ lit,
                                             const uint64_t *__restrict__ blk_tok,
@@ -125,7 +140,7 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
                                         (uint32_t)(src >> 32) | (ml << 8)));
         }
         // literal runs: sources in the literal array, always independent
-        group_copy<G, kUnrollWave>(g, out, dl, lit + (lbase + lincl - ll), ll);
+        group_copy<G, UW>(g, out, dl, lit + (lbase + lincl - ll), ll);
         g.sync();
         // in-order matches, batched so no batch reads what it writes
         const bool m0 = v && ml && tag == 0;
@@ -138,7 +153,7 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
             const unsigned lim = dmask & (0u - dmask);
             const unsigned batch = lim ? (rem & (lim - 1u)) : rem;
             const bool mine = (batch >> g.lane) & 1u;
-            group_copy<G, kUnrollWave>(g, out, dm, out + src, mine ? ml : 0u);
+            group_copy<G, UW>(g, out, dm, out + src, mine ? ml : 0u);
             g.sync();
             rem &= ~batch;
         }
@@ -150,7 +165,7 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
 // Wave 0 of every block, one group per block.  With done non-null (the
 // persistent schedule follows), each block's done bits start as its empty
 // waves plus wave 0.
-template <int G>
+template <int G, int UW>
 __global__ void __launch_bounds__(kThreads, 3) k_wave0(const uint4 *__restrict__ tok,
                                                        const uint8_t *__restrict__ lit,
                                                        const uint64_t *__restrict__ blk_tok,
@@ -160,9 +175,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_wave0(const uint4 *__restrict__
                                                        uint32_t log2bs, const uint64_t *__restrict__ pending,
                                                        uint64_t *done, uint32_t ww) {
     Group<G> g;
+    griddep_launch_dependents();
     const uint32_t b = (uint32_t)((blockIdx.x * (uint64_t)kThreads + threadIdx.x) / G);
     if (b >= nb) return;
-    block_wave0<G>(g, b, tok, lit, blk_tok, blk_lit, slot, tri, out, log2bs);
+    block_wave0<G, UW>(g, b, tok, lit, blk_tok, blk_lit, slot, tri, out, log2bs);
     if (done)
         for (uint32_t k = g.lane; k < ww; k += G)
             done[(uint64_t)b * ww + k] = ~__ldg(pending + (uint64_t)b * ww + k) | (k == 0 ? 1ULL : 0ULL);
@@ -303,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, STAGED ? 2 : 3)
                             return;  // a bulk copy did not complete: no further copies into the stage
                     }
                 } else {
-                    group_copy<G, kUnrollCopy>(g, out, d, out + sr, mine ? len : 0u);
+                    group_copy<G, kUnrollRanges>(g, out, d, out + sr, mine ? len : 0u);
                 }
                 g.sync();
                 rem &= ~batch;
@@ -370,6 +386,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_wave_copy(const uint4 *__restri
                                                         uint8_t *out, uint32_t log2bs) {
     Group<G> g;
     constexpr uint64_t T = (uint64_t)G * ITEMS;
+    griddep_launch_dependents();
     const uint64_t gid = (blockIdx.x * (uint64_t)kThreads + threadIdx.x) / G;
     const uint64_t a = gid * T;
     if (a >= n) return;
@@ -387,15 +404,24 @@ __global__ void __launch_bounds__(kThreads, 3) k_wave_copy(const uint4 *__restri
         if (m) { s = w + (uint64_t)(__ffs(m) - 1); break; }
     }
     if (s == ~0ULL) return;
+    // the next window's triplets are loaded while the current one is copied;
+    // lane 0 takes the block of the triplet before its window from the last
+    // lane of the previous window (every lane of which was valid)
+    uint4 nt = s + g.lane < n ? __ldg(tri + s + g.lane) : make_uint4(0, 0, 0, 0);
+    uint64_t prev_blk = ~0ULL;
+    // the worklist was written at upload; the sources, by earlier waves
+    griddep_wait();
     for (uint64_t cur = s; cur < n; cur += G) {
         const uint64_t i = cur + g.lane;
         const bool v = i < n;
-        const uint4 t = v ? __ldg(tri + i) : make_uint4(0, 0, 0, 0);
+        const uint4 t = v ? nt : make_uint4(0, 0, 0, 0);
+        if (cur + G + g.lane < n) nt = __ldg(tri + cur + G + g.lane);
         const uint64_t d = tri_dst(t), sr = tri_src(t);
         const uint32_t len = v ? tri_len(t) : 0u;
         const uint64_t blk = d >> log2bs;
         uint64_t pblk = g.shfl_up(blk, 1);
-        if (g.lane == 0) pblk = (i == s || i == 0) ? ~0ULL : (tri_dst(__ldg(tri + i - 1)) >> log2bs);
+        if (g.lane == 0) pblk = (i == s) ? ~0ULL : prev_blk;
+        prev_blk = g.shfl(blk, G - 1);
         const bool st = v && (i == s || blk != pblk);
         const unsigned stop = g.ballot(st && i >= e && i != s);
         unsigned act = g.ballot(v);
@@ -428,9 +454,9 @@ template <int G>
 int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st, cudaEvent_t phase) {
     constexpr int gpc = kThreads / G;  // groups per CTA
     const unsigned grid0 = (h->n_blocks + gpc - 1) / gpc;
-    k_wave0<G><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
-                                            h->d_blk_lit, h->d_slot, nullptr, out,
-                                            h->n_blocks, h->log2_bs, nullptr, nullptr, 0);
+    k_wave0<G, kUnrollWaveShort><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
+                                                              h->d_blk_lit, h->d_slot, nullptr, out,
+                                                              h->n_blocks, h->log2_bs, nullptr, nullptr, 0);
     if (phase) cudaEventRecord(phase, st);
     constexpr int ITEMS = 2;
     // deferred matches of three or more 16-byte chunks on average: full
@@ -446,14 +472,25 @@ int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st, cudaEvent_t phas
         const uint64_t groups = (n + per - 1) / per;
         const unsigned grid = (unsigned)((groups + gpc - 1) / gpc);
         const uint4 *t = (const uint4 *)h->d_tri + a;
-        if (small && ff)
-            k_wave_copy<G, 1, true><<<grid, kThreads, 0, st>>>(t, n, out, h->log2_bs);
-        else if (small)
-            k_wave_copy<G, 1, false><<<grid, kThreads, 0, st>>>(t, n, out, h->log2_bs);
-        else if (ff)
-            k_wave_copy<G, ITEMS, true><<<grid, kThreads, 0, st>>>(t, n, out, h->log2_bs);
-        else
-            k_wave_copy<G, ITEMS, false><<<grid, kThreads, 0, st>>>(t, n, out, h->log2_bs);
+        auto k = small ? (ff ? k_wave_copy<G, 1, true> : k_wave_copy<G, 1, false>)
+                       : (ff ? k_wave_copy<G, ITEMS, true> : k_wave_copy<G, ITEMS, false>);
+        // programmatic stream serialization: this wave's CTAs may start (and
+        // load their worklist) while the previous kernel's last CTAs finish
+        cudaLaunchConfig_t lc = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = kWavePdl;
+        lc.gridDim = dim3(grid);
+        lc.blockDim = dim3(kThreads);
+        lc.dynamicSmemBytes = 0;
+        lc.stream = st;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        uint32_t lb = h->log2_bs;
+        if (cudaError_t e = cudaLaunchKernelEx(&lc, k, t, n, out, lb); e != cudaSuccess) {
+            note_cuda_error(e);
+            return ACLZ_E_CUDA;
+        }
     }
     if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
         note_cuda_error(e);
@@ -482,10 +519,10 @@ template <int G, bool STAGED>
 int launch_persistent(aclz_handle *h, uint8_t *out, uint32_t ctas_per_sm, cudaStream_t st, cudaEvent_t phase) {
     constexpr int gpc = kThreads / G;
     const unsigned grid0 = (h->n_blocks + gpc - 1) / gpc;
-    k_wave0<G><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
-                                            h->d_blk_lit, h->d_slot, nullptr, out,
-                                            h->n_blocks, h->log2_bs, h->d_pending, h->d_done,
-                                            h->n_wave_words);
+    k_wave0<G, kUnrollWaveLong><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
+                                                             h->d_blk_lit, h->d_slot, nullptr, out,
+                                                             h->n_blocks, h->log2_bs, h->d_pending, h->d_done,
+                                                             h->n_wave_words);
     if (phase) cudaEventRecord(phase, st);
     if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
         note_cuda_error(e);
