@@ -44,14 +44,15 @@ constexpr int kUnrollRanges = 4; // the same in the persistent schedule's regist
 constexpr uint32_t kTmaMin = 192;
 constexpr uint32_t kPiece = 2048;
 constexpr uint32_t kSmemPerSm = 220u * 1024u;  // stage memory shared by the CTAs of one SM
-// waves with fewer triplets than about 152 SMs x 16 groups x 64 go one
-// window per group
-constexpr uint64_t kSmallWave = 155648;
 // per-wave copies put full chunks first when deferred matches average
 // at least this many bytes
 constexpr double kFullFirstMin = 48.0;
 // per-wave kernels are launched with programmatic stream serialization
 constexpr int kWavePdl = 1;
+// wave 0 reads literals through the non-coherent L1 path; before
+// per-wave copies (short tokens) it also prefetches the next window's
+// literal lines into L1 and the tokens two windows ahead into L2
+constexpr bool kWave0Ro = true;
 
 __device__ __forceinline__ uint64_t tri_dst(const uint4 t) { return (uint64_t)t.x | ((uint64_t)(t.y & 0xffu) << 32); }
 __device__ __forceinline__ uint64_t tri_src(const uint4 t) { return (uint64_t)t.z | ((uint64_t)(t.w & 0xffu) << 32); }
@@ -104,7 +105,7 @@ __device__ __forceinline__ bool wait_waves_below(const unsigned long long *done,
 // Wave 0 of one block: scan, literal runs, in-order (tag 0) matches, and
 // the deferred matches' triplets.  The next window's tokens are loaded
 // while the current window is copied.
-template <int G, int UW>
+template <int G, int UW, bool PF>
 __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const uint4 *__restrict__ tok,
                                             const uint8_t *__restrict__ lit,
                                             const uint64_t *__restrict__ blk_tok,
@@ -113,6 +114,7 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
                                             uint32_t log2bs) {
     const uint64_t t0 = blk_tok[b], t1 = blk_tok[b + 1];
     uint64_t lbase = blk_lit[b];
+    const uint64_t lend = blk_lit[b + 1];
     uint64_t pos = (uint64_t)b << log2bs;
     // the next window's tokens and worklist slots are loaded while the
     // current window is copied
@@ -140,7 +142,13 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
                                         (uint32_t)(src >> 32) | (ml << 8)));
         }
         // literal runs: sources in the literal array, always independent
-        group_copy<G, UW>(g, out, dl, lit + (lbase + lincl - ll), ll);
+        if (PF) {  // addresses inside this block's literals and tokens only
+            const uint64_t nl = lbase + g.shfl(lincl, G - 1) + 128 * g.lane;
+            if (g.lane < 2 && nl < lend) asm volatile("prefetch.global.L1 [%0];" ::"l"(lit + nl));
+            const uint64_t nt2 = w + 2 * G + 8 * (g.lane - 4);
+            if (g.lane >= 4 && g.lane < 8 && nt2 < t1) asm volatile("prefetch.global.L2 [%0];" ::"l"(tok + nt2));
+        }
+        group_copy<G, UW, false, kWave0Ro>(g, out, dl, lit + (lbase + lincl - ll), ll);
         g.sync();
         // in-order matches, batched so no batch reads what it writes
         const bool m0 = v && ml && tag == 0;
@@ -165,7 +173,7 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
 // Wave 0 of every block, one group per block.  With done non-null (the
 // persistent schedule follows), each block's done bits start as its empty
 // waves plus wave 0.
-template <int G, int UW>
+template <int G, int UW, bool PF>
 __global__ void __launch_bounds__(kThreads, 3) k_wave0(const uint4 *__restrict__ tok,
                                                        const uint8_t *__restrict__ lit,
                                                        const uint64_t *__restrict__ blk_tok,
@@ -178,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_wave0(const uint4 *__restrict__
     griddep_launch_dependents();
     const uint32_t b = (uint32_t)((blockIdx.x * (uint64_t)kThreads + threadIdx.x) / G);
     if (b >= nb) return;
-    block_wave0<G, UW>(g, b, tok, lit, blk_tok, blk_lit, slot, tri, out, log2bs);
+    block_wave0<G, UW, PF>(g, b, tok, lit, blk_tok, blk_lit, slot, tri, out, log2bs);
     if (done)
         for (uint32_t k = g.lane; k < ww; k += G)
             done[(uint64_t)b * ww + k] = ~__ldg(pending + (uint64_t)b * ww + k) | (k == 0 ? 1ULL : 0ULL);
@@ -454,26 +462,23 @@ template <int G>
 int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st, cudaEvent_t phase) {
     constexpr int gpc = kThreads / G;  // groups per CTA
     const unsigned grid0 = (h->n_blocks + gpc - 1) / gpc;
-    k_wave0<G, kUnrollWaveShort><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
+    k_wave0<G, kUnrollWaveShort, true><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
                                                               h->d_blk_lit, h->d_slot, nullptr, out,
                                                               h->n_blocks, h->log2_bs, nullptr, nullptr, 0);
     if (phase) cudaEventRecord(phase, st);
-    constexpr int ITEMS = 2;
+    // one window of G triplets per group: the most resident groups per wave
+    constexpr int ITEMS = 1;
     // deferred matches of three or more 16-byte chunks on average: full
     // chunks first
     const bool ff = h->mean_deferred_len >= (double)kFullFirstMin;
     for (uint32_t w = 1; w < h->n_waves; w++) {
         const uint64_t a = h->wave_start[w], n = h->wave_start[w + 1] - a;
         if (!n) continue;
-        // small waves: one window of G triplets per group, so more groups
-        // share the wave (about one full round of the GPU's resident groups)
-        const bool small = n < kSmallWave;
-        const uint64_t per = (uint64_t)G * (small ? 1 : ITEMS);
+        const uint64_t per = (uint64_t)G * ITEMS;
         const uint64_t groups = (n + per - 1) / per;
         const unsigned grid = (unsigned)((groups + gpc - 1) / gpc);
         const uint4 *t = (const uint4 *)h->d_tri + a;
-        auto k = small ? (ff ? k_wave_copy<G, 1, true> : k_wave_copy<G, 1, false>)
-                       : (ff ? k_wave_copy<G, ITEMS, true> : k_wave_copy<G, ITEMS, false>);
+        auto k = ff ? k_wave_copy<G, ITEMS, true> : k_wave_copy<G, ITEMS, false>;
         // programmatic stream serialization: this wave's CTAs may start (and
         // load their worklist) while the previous kernel's last CTAs finish
         cudaLaunchConfig_t lc = {};
@@ -519,7 +524,7 @@ template <int G, bool STAGED>
 int launch_persistent(aclz_handle *h, uint8_t *out, uint32_t ctas_per_sm, cudaStream_t st, cudaEvent_t phase) {
     constexpr int gpc = kThreads / G;
     const unsigned grid0 = (h->n_blocks + gpc - 1) / gpc;
-    k_wave0<G, kUnrollWaveLong><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
+    k_wave0<G, kUnrollWaveLong, false><<<grid0, kThreads, 0, st>>>((const uint4 *)h->d_tok, h->d_lit, h->d_blk_tok,
                                                              h->d_blk_lit, h->d_slot, nullptr, out,
                                                              h->n_blocks, h->log2_bs, h->d_pending, h->d_done,
                                                              h->n_wave_words);

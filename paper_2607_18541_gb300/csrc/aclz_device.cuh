@@ -109,8 +109,10 @@ __device__ __forceinline__ void store_partial16(uint8_t *p, uint4 v, uint32_t lo
 // output byte A + lo).  Only the aligned source words holding needed bytes
 // are read, so reads never leave the 16-byte words of the source range.
 // SMEM: the source is a shared-memory staging copy whose addresses are
-// congruent mod 16 to the global source.
-template <bool SMEM>
+// congruent mod 16 to the global source.  RO: the source is global memory
+// that no thread writes during the kernel (the literal array), read through
+// the non-coherent L1 path.
+template <bool SMEM, bool RO = false>
 __device__ __forceinline__ void chunk_load(const uint8_t *s, uint32_t lo, uint32_t hi, uint4 &w0, uint4 &w1,
                                            uint32_t &r) {
     const uintptr_t vs = reinterpret_cast<uintptr_t>(s) - lo;
@@ -123,6 +125,9 @@ __device__ __forceinline__ void chunk_load(const uint8_t *s, uint32_t lo, uint32
     if (SMEM) {
         if (base + 16 > s0) w0 = lds16(reinterpret_cast<const uint8_t *>(base));
         if (s1 > base + 16) w1 = lds16(reinterpret_cast<const uint8_t *>(base + 16));
+    } else if (RO) {
+        if (base + 16 > s0) w0 = __ldg(reinterpret_cast<const uint4 *>(base));
+        if (s1 > base + 16) w1 = __ldg(reinterpret_cast<const uint4 *>(base + 16));
     } else {
         if (base + 16 > s0) w0 = ldcg16(reinterpret_cast<const uint8_t *>(base));
         if (s1 > base + 16) w1 = ldcg16(reinterpret_cast<const uint8_t *>(base + 16));
@@ -155,7 +160,7 @@ __device__ __forceinline__ int owner_lane(const Group<G> &g, uint32_t incl, uint
 // chunks (c per lane, inclusive prefix incl, total in all) are numbered in
 // lane order and dealt to the group's lanes, U per lane per round, loads
 // issued before stores.
-template <int G, int U, bool SMEM>
+template <int G, int U, bool SMEM, bool RO = false>
 __device__ __forceinline__ void copy_chunks_in_order(const Group<G> &g, uint8_t *out, uint64_t d,
                                                      const uint8_t *s, uint32_t n, uint32_t c,
                                                      uint32_t incl, uint32_t total) {
@@ -183,7 +188,7 @@ __device__ __forceinline__ void copy_chunks_in_order(const Group<G> &g, uint8_t 
             dst[u] = out + A;
             if (k < total) {
                 lohi[u] = clo | (chi << 8);
-                chunk_load<SMEM>(sj + (blo - dj), clo, chi, a[u], b[u], r[u]);
+                chunk_load<SMEM, RO>(sj + (blo - dj), clo, chi, a[u], b[u], r[u]);
             }
         }
 #pragma unroll
@@ -273,13 +278,13 @@ __device__ __forceinline__ void copy_chunks_full_first(const Group<G> &g, uint8_
 // deals every job's full chunks first, for match copies of a few chunks or
 // more.  Jobs must be independent: no job's source may overlap another
 // job's output in the same call.
-template <int G, int U, bool SMEM = false>
+template <int G, int U, bool SMEM = false, bool RO = false>
 __device__ __forceinline__ void group_copy(const Group<G> &g, uint8_t *out, uint64_t d,
                                            const uint8_t *s, uint32_t n) {
     const uint32_t c = n ? (uint32_t)(((d + n - 1) >> 4) - (d >> 4) + 1) : 0u;
     const uint32_t incl = g.scan_incl(c);
     const uint32_t total = g.shfl(incl, G - 1);
-    copy_chunks_in_order<G, U, SMEM>(g, out, d, s, n, c, incl, total);
+    copy_chunks_in_order<G, U, SMEM, RO>(g, out, d, s, n, c, incl, total);
 }
 
 template <int G, int U, bool SMEM = false>
