@@ -38,7 +38,7 @@ constexpr int kThreads = 256;
 // (short matches; more resident warps without spills) and before the
 // persistent schedule (long in-order matches)
 constexpr int kUnrollWaveShort = 1, kUnrollWaveLong = 2;
-constexpr int kUnrollCopy = 2;   // chunks per lane per round in per-wave match copies
+constexpr int kUnrollCopy = 3;   // chunks per lane per round in per-wave match copies
 constexpr int kUnrollRanges = 4; // the same in the persistent schedule's register copies
 // staged (TMA) copies: jobs of at least kTmaMin bytes, pieces of <= kPiece
 constexpr uint32_t kTmaMin = 192;
