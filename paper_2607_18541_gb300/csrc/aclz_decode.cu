@@ -57,6 +57,9 @@ constexpr bool kWave0Ro = true;
 __device__ __forceinline__ uint64_t tri_dst(const uint4 t) { return (uint64_t)t.x | ((uint64_t)(t.y & 0xffu) << 32); }
 __device__ __forceinline__ uint64_t tri_src(const uint4 t) { return (uint64_t)t.z | ((uint64_t)(t.w & 0xffu) << 32); }
 __device__ __forceinline__ uint32_t tri_len(const uint4 t) { return t.w >> 8; }
+// set at upload on the triplets of segments without an internal chain: a
+// per-wave group may start or stop at any of them
+__device__ __forceinline__ bool tri_cut(const uint4 t) { return (t.y >> 8) & 1u; }
 
 __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
     unsigned long long v;
@@ -98,6 +101,27 @@ __device__ __forceinline__ bool wait_waves_below(const unsigned long long *done,
         }
     }
     return true;
+}
+
+// Exact same-wave dependencies inside one window of triplets (one per
+// lane): bit j of the result is set when this lane's source overlaps the
+// output of lane j < this lane.  Only matches of one block can depend on
+// each other within a wave (a source in another block was final a wave
+// earlier), so lanes whose source does not end in their own block skip the
+// test.
+template <int G>
+__device__ __forceinline__ unsigned same_wave_deps(const Group<G> &g, bool v, uint64_t d, uint64_t sr,
+                                                   uint32_t len, uint32_t log2bs) {
+    const uint64_t blk = d >> log2bs;
+    const bool local = v && ((sr + len - 1) >> log2bs) == blk;
+    unsigned m = 0;
+    if (!g.ballot(local)) return 0u;
+    for (int j = 0; j < G; j++) {
+        const uint64_t dj = g.shfl(d, j);
+        const uint32_t nj = g.shfl(len, j);
+        if (local && j < g.lane && nj && (dj >> log2bs) == blk && sr < dj + nj && dj < sr + len) m |= 1u << j;
+    }
+    return m;
 }
 
 // ------------------------------------------------------------- wave 0
@@ -193,27 +217,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_wave0(const uint4 *__restrict__
 }
 
 // ------------------------------------------------ persistent schedule
-
-// Exact same-wave dependencies inside one window of triplets (one per
-// lane): bit j of the result is set when this lane's source overlaps the
-// output of lane j < this lane.  Only matches of one block can depend on
-// each other within a wave (a source in another block was final a wave
-// earlier), so lanes whose source does not end in their own block skip the
-// test.
-template <int G>
-__device__ __forceinline__ unsigned same_wave_deps(const Group<G> &g, bool v, uint64_t d, uint64_t sr,
-                                                   uint32_t len, uint32_t log2bs) {
-    const uint64_t blk = d >> log2bs;
-    const bool local = v && ((sr + len - 1) >> log2bs) == blk;
-    unsigned m = 0;
-    if (!g.ballot(local)) return 0u;
-    for (int j = 0; j < G; j++) {
-        const uint64_t dj = g.shfl(d, j);
-        const uint32_t nj = g.shfl(len, j);
-        if (local && j < g.lane && nj && (dj >> log2bs) == blk && sr < dj + nj && dj < sr + len) m |= 1u << j;
-    }
-    return m;
-}
 
 // One look, without waiting, at whether every block of [sr, sr + len) has
 // finished its waves below w (w <= 64, at most 4 blocks); acquire loads.
@@ -399,14 +402,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_wave_copy(const uint4 *__restri
     const uint64_t a = gid * T;
     if (a >= n) return;
     const uint64_t e = a + T < n ? a + T : n;
-    // first segment start in [a, e)
+    // first cut point in [a, e): a segment start, or any triplet of a
+    // segment without an internal chain
     uint64_t s = ~0ULL;
     for (uint64_t w = a; w < e; w += G) {
         const uint64_t i = w + g.lane;
         bool st = false;
         if (i < e) {
-            const uint64_t bi = tri_dst(__ldg(tri + i)) >> log2bs;
-            st = (i == 0) || (bi != (tri_dst(__ldg(tri + i - 1)) >> log2bs));
+            const uint4 ti = __ldg(tri + i);
+            const uint64_t bi = tri_dst(ti) >> log2bs;
+            st = (i == 0) || tri_cut(ti) || (bi != (tri_dst(__ldg(tri + i - 1)) >> log2bs));
         }
         const unsigned m = g.ballot(st);
         if (m) { s = w + (uint64_t)(__ffs(m) - 1); break; }
@@ -430,22 +435,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_wave_copy(const uint4 *__restri
         uint64_t pblk = g.shfl_up(blk, 1);
         if (g.lane == 0) pblk = (i == s) ? ~0ULL : prev_blk;
         prev_blk = g.shfl(blk, G - 1);
-        const bool st = v && (i == s || blk != pblk);
+        const bool st = v && (i == s || blk != pblk || tri_cut(t));
         const unsigned stop = g.ballot(st && i >= e && i != s);
         unsigned act = g.ballot(v);
         if (stop) act &= (stop & (0u - stop)) - 1u;
-        const unsigned S = g.ballot(st);
+        // exact same-wave dependencies inside the window (only sources that
+        // end in their own block can have any); each batch takes the lanes
+        // whose dependencies are all copied
+        const unsigned deps = same_wave_deps<G>(g, (act >> g.lane) & 1u, d, sr, len, log2bs) & act;
         unsigned rem = act;
         while (rem) {
-            const int f = __ffs(rem) - 1;
-            const unsigned upto = (g.lane == G - 1) ? 0xffffffffu : ((2u << g.lane) - 1u);
-            const unsigned sm = (S | (1u << f)) & ~((1u << f) - 1u) & upto;
-            const int fs = sm ? 31 - __clz(sm) : f;
-            const uint64_t fsd = g.shfl(d, fs);
-            const bool dep = ((rem >> g.lane) & 1u) && g.lane > fs && (sr + len > fsd);
-            const unsigned dmask = g.ballot(dep);
-            const unsigned lim = dmask & (0u - dmask);
-            const unsigned batch = lim ? (rem & (lim - 1u)) : rem;
+            const unsigned batch = g.ballot(((rem >> g.lane) & 1u) && (deps & rem) == 0u);
             const bool mine = (batch >> g.lane) & 1u;
             if (FULL_FIRST)
                 group_copy_full_first<G, kUnrollCopy>(g, out, d, out + sr, mine ? len : 0u);

@@ -510,6 +510,16 @@ __global__ void k_seg_dep(const uint4 *__restrict__ tri, const uint4 *__restrict
     }
 }
 
+// Bit 8 of a triplet's .y (above its destination's high byte) marks the
+// triplets of segments without an internal chain: the per-wave kernel may
+// cut such a segment between groups at any triplet.
+__global__ void k_tri_cuttable(uint4 *tri, const uint32_t *__restrict__ seg_of, const uint32_t *__restrict__ segdep,
+                               uint64_t n) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n;
+         t += (uint64_t)gridDim.x * blockDim.x)
+        tri[t].y = (tri[t].y & 0xffu) | (segdep[seg_of[t]] ? 0u : 0x100u);
+}
+
 // Range starts.  In wave w (triplets from wstart[w]) a range starts every
 // wT[w] triplets, except inside a segment with an internal chain, whose
 // candidate starts move to the end of that segment.
@@ -1062,6 +1072,7 @@ extern "C" int aclz_set_range_bytes(aclz_handle *h, uint32_t range_bytes, void *
     if (rc) return rc;
     k_seg_of<<<gseg, 256, 0, st>>>(seg, nseg, seg_of);
     k_seg_dep<<<grid, 256, 0, st>>>((const uint4 *)h->d_tri, seg, seg_of, n, segdep);
+    k_tri_cuttable<<<grid, 256, 0, st>>>((uint4 *)h->d_tri, seg_of, segdep, n);
     k_range_flags<<<grid, 256, 0, st>>>(seg, seg_of, segdep, (const uint64_t *)b_ws.p, (const uint32_t *)b_wT.p, n,
                                          flag);
     ck(cudaGetLastError());
