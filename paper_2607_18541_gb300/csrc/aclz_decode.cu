@@ -174,16 +174,15 @@ __device__ __forceinline__ void block_wave0(const Group<G> &g, uint32_t b, const
         }
         group_copy<G, UW, false, kWave0Ro>(g, out, dl, lit + (lbase + lincl - ll), ll);
         g.sync();
-        // in-order matches, batched so no batch reads what it writes
+        // in-order matches, batched so no batch reads what it writes: each
+        // batch takes the lanes whose sources overlap no output of a lane
+        // still to be copied (exact pairwise overlaps; the sources of
+        // in-order matches lie in their own block)
         const bool m0 = v && ml && tag == 0;
         unsigned rem = g.ballot(m0);
+        const unsigned deps0 = rem ? same_wave_deps<G>(g, m0, dm, src, ml, log2bs) & rem : 0u;
         while (rem) {
-            const int f = __ffs(rem) - 1;
-            const uint64_t fd = g.shfl(dm, f);
-            const bool dep = m0 && ((rem >> g.lane) & 1u) && g.lane > f && (src + ml > fd);
-            const unsigned dmask = g.ballot(dep);
-            const unsigned lim = dmask & (0u - dmask);
-            const unsigned batch = lim ? (rem & (lim - 1u)) : rem;
+            const unsigned batch = g.ballot(((rem >> g.lane) & 1u) && (deps0 & rem) == 0u);
             const bool mine = (batch >> g.lane) & 1u;
             group_copy<G, UW>(g, out, dm, out + src, mine ? ml : 0u);
             g.sync();
