@@ -34,6 +34,9 @@ using namespace aclz;
 namespace {
 
 constexpr int kThreads = 256;
+// per-wave copy CTAs, and the CTAs of that size per SM the register cap
+// is set for (the same 85 registers a thread as 3 x 256)
+constexpr int kWaveThreads = 64, kWaveMinCtas = 768 / kWaveThreads;
 // chunks per lane per round in the wave-0 pass: before per-wave copies
 // (short matches; more resident warps without spills) and before the
 // persistent schedule (long in-order matches)
@@ -392,12 +395,12 @@ __global__ void __launch_bounds__(kThreads, STAGED ? 2 : 3)
 // 16-byte chunks are copied before their partial ones (for matches of
 // several chunks); otherwise chunks go in match order.
 template <int G, int ITEMS, bool FULL_FIRST>
-__global__ void __launch_bounds__(kThreads, 3) k_wave_copy(const uint4 *__restrict__ tri, uint64_t n,
+__global__ void __launch_bounds__(kWaveThreads, kWaveMinCtas) k_wave_copy(const uint4 *__restrict__ tri, uint64_t n,
                                                         uint8_t *out, uint32_t log2bs) {
     Group<G> g;
     constexpr uint64_t T = (uint64_t)G * ITEMS;
     griddep_launch_dependents();
-    const uint64_t gid = (blockIdx.x * (uint64_t)kThreads + threadIdx.x) / G;
+    const uint64_t gid = (blockIdx.x * (uint64_t)kWaveThreads + threadIdx.x) / G;
     const uint64_t a = gid * T;
     if (a >= n) return;
     const uint64_t e = a + T < n ? a + T : n;
@@ -475,7 +478,8 @@ int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st, cudaEvent_t phas
         if (!n) continue;
         const uint64_t per = (uint64_t)G * ITEMS;
         const uint64_t groups = (n + per - 1) / per;
-        const unsigned grid = (unsigned)((groups + gpc - 1) / gpc);
+        constexpr int gpcw = kWaveThreads / G;
+        const unsigned grid = (unsigned)((groups + gpcw - 1) / gpcw);
         const uint4 *t = (const uint4 *)h->d_tri + a;
         auto k = ff ? k_wave_copy<G, ITEMS, true> : k_wave_copy<G, ITEMS, false>;
         // programmatic stream serialization: this wave's CTAs may start (and
@@ -485,7 +489,7 @@ int launch_waves(aclz_handle *h, uint8_t *out, cudaStream_t st, cudaEvent_t phas
         at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         at[0].val.programmaticStreamSerializationAllowed = kWavePdl;
         lc.gridDim = dim3(grid);
-        lc.blockDim = dim3(kThreads);
+        lc.blockDim = dim3(kWaveThreads);
         lc.dynamicSmemBytes = 0;
         lc.stream = st;
         lc.attrs = at;
