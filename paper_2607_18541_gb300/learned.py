@@ -501,26 +501,32 @@ def train_default(scale: int = 1, steps: int = 2000, seed: int = 20260712, log=p
     return _fit(f, y, coef, seed, steps, log)
 
 
-def train_selected(streams, val, seeds=(20260712, 1, 2, 3, 4, 5), steps: int = 800, log=print):
+def train_selected(streams, val, seeds=(20260712, 1, 2, 3, 4, 5), steps: int = 800, log=print,
+                   tries: int = 2, want: float = 1.02):
     """Networks from one set of labels with different initialisations and
     batch orders; the one returned is the one whose picks, through the full
     check (size, modelled time and a measured decode), decode the
     validation stream `val` (not used for training) fastest, measured,
     relative to 12/16/24/32 on that stream.  A network that lands on
     12/16/24/32 for every block gains nothing there and loses to any that
-    keeps useful picks."""
-    f, y, coef = _time_labelled(streams, log)
+    keeps useful picks.  The labels rest on measured decode times; when no
+    initialisation reaches `want` on the validation stream, the labels are
+    measured again (up to `tries` times) and the best over all is kept."""
     fbv = encode(val, CANDIDATES[FALLBACK])
     g_fb = decode_gbs(fbv, val.size, reps=7)[0]
     judge = lambda c: val.size / decode_gbs(c, val.size, reps=7)[0] / 1e6
     best, best_gain = None, -1.0
-    for sd in seeds:
-        m = _fit(f, y, coef, sd, steps, log)
-        cv, kv = encode_learned(m, val, fb=fbv, time_coef=coef, judge=judge)
-        gain = decode_gbs(cv, val.size, reps=7)[0] / g_fb if np.any(kv != FALLBACK) else 1.0
-        log(json.dumps({"seed": sd, "val_kept": float(np.mean(kv != FALLBACK)), "val_gain": round(gain, 4)}))
-        if gain > best_gain:
-            best, best_gain = m, gain
+    for _ in range(tries):
+        f, y, coef = _time_labelled(streams, log)
+        for sd in seeds:
+            m = _fit(f, y, coef, sd, steps, log)
+            cv, kv = encode_learned(m, val, fb=fbv, time_coef=coef, judge=judge)
+            gain = decode_gbs(cv, val.size, reps=7)[0] / g_fb if np.any(kv != FALLBACK) else 1.0
+            log(json.dumps({"seed": sd, "val_kept": float(np.mean(kv != FALLBACK)), "val_gain": round(gain, 4)}))
+            if gain > best_gain:
+                best, best_gain = m, gain
+        if best_gain >= want:
+            break
     return best
 
 
